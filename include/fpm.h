@@ -1,0 +1,259 @@
+/*
+ * fpm.h -- C ABI of the B300 (sm_103a) Fourier ptychographic microscopy (FPM)
+ * tile-reconstruction library.
+ *
+ * What it computes (the paper, "Parallel Fourier Ptychography reconstruction"):
+ *   the sensor field of view is cut into overlapping square sub-regions (tiles,
+ *   Sec. 3.1, Fig. 5) that are reconstructed independently; each tile sees every
+ *   LED at its own illumination angle (Sec. 2.2, Fig. 3/4) and has its own
+ *   defocus (Sec. 2.2).  A tile's high-resolution (HR) spectrum is recovered by
+ *   alternating projection (Sec. 2.1, Fig. 2): for each LED in the update order
+ *   (Sec. 3.2, Fig. 6) the shifted sub-aperture of the spectrum is cut out and
+ *   multiplied by the pupil, inverse transformed to the low-resolution (LR)
+ *   grid, given the measured amplitude, transformed back, and written into the
+ *   spectrum; with FPM_EPRY the pupil is corrected too (embedded pupil recovery,
+ *   Ou, Zheng and Yang, Opt. Express 22(5):4960, 2014).  LEDs whose sub-apertures
+ *   do not share a spectrum pixel are updated concurrently in "waves" (the
+ *   spectrum-domain parallelism of Sec. 3.2).
+ *
+ * Conventions used by every entry point:
+ *   - Return value: FPM_OK (0) or a negative FPM_E* status.  On failure nothing
+ *     the caller owns has been modified and fpm_last_error() (thread-local)
+ *     describes the cause.  No C++ exception crosses the ABI.
+ *   - Complex numbers are complex64: interleaved (re, im) float32 pairs.
+ *   - Spectra are "centred": element (y, x) of an N x N array holds spatial
+ *     frequency (y - N/2, x - N/2) Fourier pixels; the DC term sits at (N/2, N/2).
+ *     Pupils are m x m, centred the same way.  All 2-D arrays are row-major.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = the legacy
+ *     default stream).  Calls that take a stream only enqueue work on it; the
+ *     caller synchronises.
+ *   - A plan is not thread-safe: one thread at a time may use it.  A server is
+ *     thread-safe.
+ *   - Device memory the library allocates belongs to the plan (or server) and is
+ *     freed by fpm_plan_destroy (fpm_server_destroy).
+ */
+#ifndef FPM_H_
+#define FPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FPM_API __attribute__((visibility("default")))
+#else
+#define FPM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define FPM_OK         0
+#define FPM_EINVAL    (-1)  /* bad argument or geometry                          */
+#define FPM_ENOMEM    (-2)  /* host or device allocation failed                  */
+#define FPM_EBUDGET   (-3)  /* the job can never fit the server's HBM budget     */
+#define FPM_ETIMEOUT  (-4)  /* a bounded device wait ran out (kernel returned)   */
+#define FPM_ECUDA     (-5)  /* a CUDA runtime/driver call failed                 */
+#define FPM_EBUSY     (-6)  /* the object is in use (e.g. a plan owned by a job) */
+#define FPM_ESTATE    (-7)  /* call out of order (e.g. reconstruct before load)  */
+
+/* ---- LED update routine (Sec. 3.2, Fig. 6) --------------------------------- */
+#define FPM_ORDER_CENTER_OUT 0  /* by distance of the LED from the array centre */
+#define FPM_ORDER_RASTER     1  /* LED index order                              */
+
+/* ---- plan flags ------------------------------------------------------------ */
+#define FPM_EPRY  1u  /* correct the pupil too (embedded pupil recovery)          */
+
+/* ---- image element types --------------------------------------------------- */
+#define FPM_U16 0     /* camera counts (e.g. 12-bit)                             */
+#define FPM_F32 1     /* intensities as float32                                  */
+
+/* ---- execution modes of fpm_reconstruct ------------------------------------ */
+#define FPM_RUN_PLAIN      0  /* one tile at a time, one LED per launch          */
+#define FPM_RUN_WAVES      1  /* every tile's next wave in one launch            */
+#define FPM_RUN_PERSISTENT 2  /* one persistent kernel over a device work queue  */
+#define FPM_RUN_GRAPH      0x100 /* OR-able: replay the launches as a CUDA graph */
+
+typedef struct fpm_plan fpm_plan;
+typedef struct fpm_server fpm_server;
+typedef int64_t fpm_job;
+
+/*
+ * Problem statement of one job (Sec. 2.2, Sec. 3.1, Sec. 4).  Every pointer is
+ * read during fpm_plan_create only and copied; the caller keeps ownership.
+ */
+typedef struct {
+  int32_t sensor_h, sensor_w;   /* LR sensor size in pixels                          */
+  int32_t tile;                 /* LR tile side m: 64, 128, 192 or 256                */
+  int32_t overlap;              /* LR overlap between neighbouring tiles (pixels)     */
+  int32_t tiles_y, tiles_x;     /* tile grid, centred on the sensor                   */
+  int32_t upsample;             /* N = upsample * m (HR side); 2..8                    */
+  double wavelength_um;         /* illumination wavelength                            */
+  double na;                    /* objective numerical aperture                        */
+  double pixel_um;              /* LR pixel size in the sample plane                   */
+  int32_t n_leds;               /* number of LEDs (>= 1)                               */
+  const double *led_xy_um;      /* [n_leds][2] LED (x, y) in um, optical axis at 0     */
+  double led_height_um;         /* distance between LED array and sample               */
+  const double *defocus_um;     /* [tiles_y * tiles_x] per-tile defocus, or NULL = 0   */
+  int32_t order;                /* FPM_ORDER_*                                         */
+  int32_t iters;                /* iteration loops the schedule is built for (>= 1)    */
+  uint32_t flags;               /* FPM_EPRY or 0                                        */
+} fpm_plan_desc;
+
+/* Sizes of a plan, for allocating the arrays the getters fill. */
+typedef struct {
+  int32_t m, n;                 /* LR tile side, HR side                               */
+  int32_t n_tiles, n_leds, iters;
+  int32_t support_px;           /* pixels of the circular pupil support (A)            */
+  int32_t support_rows;         /* rows of the support (R)                             */
+  int32_t max_waves;            /* largest wave count over the tiles                   */
+  int32_t max_wave_width;       /* largest number of LEDs in one wave of one tile      */
+  int64_t total_waves;          /* sum over tiles of their wave counts                 */
+  int64_t device_bytes;         /* device memory fpm_load_tiles will allocate          */
+  int32_t cluster;              /* CTAs that share one update (1 or 2)                 */
+  int32_t threads;              /* threads per CTA of the update kernel                */
+} fpm_plan_info;
+
+/*
+ * fpm_plan_create -- validate a job and compute everything that does not
+ * depend on the data (host only, FP64; no CUDA call is made):
+ *   - tile origins of the centred grid, stride tile - overlap (Sec. 3.1);
+ *   - per tile and LED the direction cosines of the line from the tile centre
+ *     to the LED and the integer sub-aperture shift
+ *     s = round_half_away(cosine / (wavelength * df)), df = 1/(m * pixel) (Sec. 2.2);
+ *   - the LED order (Sec. 3.2) and, per tile, the wave of every update in the
+ *     sequence of `iters` iteration loops: wave(j) = 0 if no earlier update's
+ *     support disc shares an HR pixel with update j's, else 1 + the largest wave
+ *     of those that do (Sec. 3.2: regions that do not affect each other are
+ *     updated in parallel, across iteration loops);
+ *   - per tile the initial pupil: circular support |f| <= NA/wavelength times
+ *     exp(i 2 pi z (sqrt(1/lambda^2 - |f|^2) - 1/lambda)) (Sec. 2.1, Sec. 2.2).
+ * Fails with FPM_EINVAL when a size is out of range, the grid does not fit the
+ * sensor, the support is too large for the tile, or a sub-aperture box would
+ * leave the N x N spectrum.
+ * On success *out owns a new plan (free it with fpm_plan_destroy).
+ */
+FPM_API int fpm_plan_create(const fpm_plan_desc *desc, fpm_plan **out);
+
+/* fpm_plan_destroy -- free a plan and its device memory (NULL is allowed).
+ * Synchronises the device first.  FPM_EBUSY if a server job still uses it. */
+FPM_API int fpm_plan_destroy(fpm_plan *plan);
+
+/* fpm_plan_get_info -- fill *info (host only). */
+FPM_API int fpm_plan_get_info(const fpm_plan *plan, fpm_plan_info *info);
+
+/*
+ * fpm_get_schedule -- copy the plan's schedule (host only).  Any pointer may be
+ * NULL to skip that array.
+ *   order   [n_leds]                    LED index visited at each position
+ *   shifts  [n_tiles][n_leds][2]        (sy, sx) per tile and LED index
+ *   waves   [n_tiles][iters * n_leds]   wave of each update of the sequence
+ *   origins [n_tiles][2]                (y0, x0) tile origin on the sensor
+ */
+FPM_API int fpm_get_schedule(const fpm_plan *plan, int32_t *order, int32_t *shifts,
+                     int32_t *waves, int32_t *origins);
+
+/*
+ * fpm_load_tiles -- attach the LR image stack and build the initial state.
+ *   stack      [n_leds][sensor_h][sensor_w] images, element type `dtype`,
+ *              element (l, y, x) at stack[l * stride_led + y * stride_row + x]
+ *              (strides in elements; rows and LED planes must start 16-byte
+ *              aligned).  Image l is the one taken with LED index l.
+ *   on_device  0: `stack` is host memory; it is copied into device memory the
+ *              plan owns (stream-ordered, the copy is complete when the stream
+ *              reaches this point).  1: `stack` is device memory the caller
+ *              keeps alive and unchanged until the plan is destroyed or loaded
+ *              again; it is read in place.
+ *   counts_per_unit  measured intensity = element / counts_per_unit (> 0).
+ * Then, per tile, the initial spectrum is the spectrum of the upsampled centre
+ * image: (N/m)^2 * zero-pad_N(centred DFT_m(sqrt(I_first))), I_first being the
+ * tile's image of the first LED of the order, and the pupil is reset to the
+ * initial pupil.  Allocates the plan's device state on first use
+ * (FPM_ENOMEM on failure).
+ */
+FPM_API int fpm_load_tiles(fpm_plan *plan, const void *stack, int32_t dtype, int32_t on_device,
+                   int64_t stride_led, int64_t stride_row, float counts_per_unit,
+                   void *stream);
+
+/*
+ * fpm_reconstruct -- run `iters` (1..plan iters) iteration loops of the per-LED
+ * update on every tile, continuing from the current state.  Per update, for
+ * the box centred at c + s of the centred spectrum O (c = N/2):
+ *   Phi  = O_box * P;  phi = (m/N)^2 IDFT_m(Phi);  phi' = sqrt(I) phi/|phi|
+ *   (sqrt(I) where phi = 0);  Phi' = (N/m)^2 DFT_m(phi');  D = Phi' - Phi;
+ *   O_box += conj(P) D / max|P|^2;  with FPM_EPRY the pupil gains
+ *   support * conj(O_box_old) D / max|O_box_old|^2 (0 if that maximum is 0).
+ * Maxima run over the pupil support.  Updates of one wave use the pupil as it
+ * was when the wave started; their pupil corrections are added in sequence
+ * order when the wave ends.  `mode` is FPM_RUN_PLAIN, FPM_RUN_WAVES or
+ * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH; all modes give the same
+ * result.  FPM_ESTATE before fpm_load_tiles; FPM_ETIMEOUT if a bounded device
+ * wait of the persistent kernel gave up (the state is then undefined).
+ */
+FPM_API int fpm_reconstruct(fpm_plan *plan, int32_t iters, int32_t mode, void *stream);
+
+/*
+ * fpm_get_spectrum / fpm_get_pupil -- copy tile `tile`'s current N x N spectrum
+ * (m x m pupil), centred complex64, to `dst` (host memory if on_device == 0,
+ * device memory otherwise).  Stream-ordered; for host `dst` the call returns
+ * after the copy completed.
+ */
+FPM_API int fpm_get_spectrum(fpm_plan *plan, int32_t tile, void *dst, int32_t on_device, void *stream);
+FPM_API int fpm_get_pupil(fpm_plan *plan, int32_t tile, void *dst, int32_t on_device, void *stream);
+
+/*
+ * fpm_set_state -- overwrite tile `tile`'s spectrum (N x N) and/or pupil (m x m)
+ * from host memory (either pointer may be NULL), e.g. to resume from a
+ * checkpoint taken with the getters.  FPM_ESTATE before fpm_load_tiles.
+ */
+FPM_API int fpm_set_state(fpm_plan *plan, int32_t tile, const void *spectrum, const void *pupil,
+                  void *stream);
+
+/* fpm_initial_pupil -- the plan's initial pupil of `tile` (host memory,
+ * m x m centred complex64; host only, no CUDA call). */
+FPM_API int fpm_initial_pupil(const fpm_plan *plan, int32_t tile, void *dst);
+
+/*
+ * fpm_simulate -- forward model (Sec. 2.1, Fig. 1) on the device, to make
+ * synthetic data: for every tile t and LED l,
+ *   I[t][l] = |(m/N)^2 IDFT_m(O_t[box(c + s_tl)] * P_t)|^2,  O_t = centred DFT_N(o_t),
+ * with P_t the plan's initial pupil.  objects: device [n_tiles][N][N] complex64
+ * HR objects o_t; out: device [n_tiles][n_leds][m][m] float32.  Allocates and
+ * frees its own temporaries; returns after the work completed.
+ */
+FPM_API int fpm_simulate(fpm_plan *plan, const void *objects, float *out, void *stream);
+
+/* ---- serving: continuous batching of many jobs ---------------------------- */
+
+/* fpm_server_create -- start a server that runs the jobs given to it on the
+ * current device, admitting them while their device memory fits
+ * `hbm_budget_bytes`.  */
+FPM_API int fpm_server_create(size_t hbm_budget_bytes, fpm_server **out);
+
+/*
+ * fpm_submit -- queue `iters` iteration loops of a loaded plan as a job
+ * (non-blocking).  The plan belongs to the server until the job is DONE or
+ * FAILED.  FPM_EBUDGET if the plan alone exceeds the budget.
+ */
+FPM_API int fpm_submit(fpm_server *server, fpm_plan *plan, int32_t iters, fpm_job *out);
+
+#define FPM_JOB_QUEUED  0
+#define FPM_JOB_RUNNING 1
+#define FPM_JOB_DONE    2
+#define FPM_JOB_FAILED  3
+
+/* fpm_poll -- current state of a job (FPM_JOB_*), and optionally its submit ->
+ * admit and submit -> done times in seconds (0 while unknown).  */
+FPM_API int fpm_poll(fpm_server *server, fpm_job job, int32_t *state, double *wait_s, double *latency_s);
+
+/* fpm_server_destroy -- finish or cancel queued jobs, stop the server, free it. */
+FPM_API int fpm_server_destroy(fpm_server *server);
+
+/* fpm_last_error -- text of the calling thread's last failure ("" if none). */
+FPM_API const char *fpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPM_H_ */

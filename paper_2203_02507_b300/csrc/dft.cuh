@@ -1,0 +1,176 @@
+// Small DFTs held entirely in registers: the butterflies of the tile FFTs.
+//
+// dft<R, S>(v) replaces v[0..R) by X[k] = sum_n v[n] exp(S * 2 pi i n k / R),
+// natural order in and out.  S = +1 is the inverse direction (no 1/R factor),
+// S = -1 the forward one.  Twiddles inside a DFT are exact constants of the
+// mathematics (cos and sin of multiples of pi/8 and pi/6), rounded to float.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fpm {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by S*i
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by (c + S i s)
+template <int S>
+__device__ __forceinline__ float2 mul_cs(float2 a, float c, float s) {
+  const float ss = S > 0 ? s : -s;
+  return make_float2(a.x * c - a.y * ss, a.x * ss + a.y * c);
+}
+
+// cos(pi/8), sin(pi/8), sqrt(1/2), sqrt(3)/2
+#define FPM_C8 0.92387953251128674f
+#define FPM_S8 0.38268343236508977f
+#define FPM_R2 0.70710678118654752f
+#define FPM_R3 0.86602540378443865f
+
+template <int S>
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+  const float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int S>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const float2 t2 = cadd(a1, a3), t3 = mul_si<S>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// X[k] = sum v[n] w^{nk}, w = exp(S 2 pi i / 3)
+template <int S>
+__device__ __forceinline__ void dft3(float2 &a0, float2 &a1, float2 &a2) {
+  const float2 s = cadd(a1, a2);
+  const float2 d = mul_si<S>(csub(a1, a2));     // S i (a1 - a2)
+  const float2 m = make_float2(a0.x - 0.5f * s.x, a0.y - 0.5f * s.y);
+  a0 = cadd(a0, s);
+  a1 = make_float2(m.x + FPM_R3 * d.x, m.y + FPM_R3 * d.y);
+  a2 = make_float2(m.x - FPM_R3 * d.x, m.y - FPM_R3 * d.y);
+}
+
+template <int R, int S>
+struct Dft;
+
+template <int S>
+struct Dft<2, S> {
+  __device__ __forceinline__ static void run(float2 *v) { dft2<S>(v[0], v[1]); }
+};
+
+template <int S>
+struct Dft<4, S> {
+  __device__ __forceinline__ static void run(float2 *v) { dft4<S>(v[0], v[1], v[2], v[3]); }
+};
+
+template <int S>
+struct Dft<3, S> {
+  __device__ __forceinline__ static void run(float2 *v) { dft3<S>(v[0], v[1], v[2]); }
+};
+
+// 8 = 2 x 4: even/odd halves, then one radix-2 stage with w8^k
+template <int S>
+struct Dft<8, S> {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<S>(e0, e1, e2, e3);
+    dft4<S>(o0, o1, o2, o3);
+    o1 = mul_cs<S>(o1, FPM_R2, FPM_R2);
+    o2 = mul_si<S>(o2);
+    o3 = mul_cs<S>(o3, -FPM_R2, FPM_R2);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+  }
+};
+
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
+template <int S>
+struct Dft<16, S> {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 y[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      float2 a0 = v[n2], a1 = v[4 + n2], a2 = v[8 + n2], a3 = v[12 + n2];
+      dft4<S>(a0, a1, a2, a3);                 // a_k1
+      y[n2 * 4 + 0] = a0;
+      y[n2 * 4 + 1] = a1;
+      y[n2 * 4 + 2] = a2;
+      y[n2 * 4 + 3] = a3;
+    }
+    // twiddles w16^{n2 k1}
+    y[1 * 4 + 1] = mul_cs<S>(y[5], FPM_C8, FPM_S8);    // w^1
+    y[1 * 4 + 2] = mul_cs<S>(y[6], FPM_R2, FPM_R2);    // w^2
+    y[1 * 4 + 3] = mul_cs<S>(y[7], FPM_S8, FPM_C8);    // w^3
+    y[2 * 4 + 1] = mul_cs<S>(y[9], FPM_R2, FPM_R2);    // w^2
+    y[2 * 4 + 2] = mul_si<S>(y[10]);                   // w^4
+    y[2 * 4 + 3] = mul_cs<S>(y[11], -FPM_R2, FPM_R2);  // w^6
+    y[3 * 4 + 1] = mul_cs<S>(y[13], FPM_S8, FPM_C8);   // w^3
+    y[3 * 4 + 2] = mul_cs<S>(y[14], -FPM_R2, FPM_R2);  // w^6
+    y[3 * 4 + 3] = mul_cs<S>(y[15], -FPM_C8, -FPM_S8); // w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 a0 = y[k1], a1 = y[4 + k1], a2 = y[8 + k1], a3 = y[12 + k1];
+      dft4<S>(a0, a1, a2, a3);                 // over n2 -> k2
+      v[k1] = a0;
+      v[k1 + 4] = a1;
+      v[k1 + 8] = a2;
+      v[k1 + 12] = a3;
+    }
+  }
+};
+
+// 12 = 3 x 4: n = 4 n1 + n2 (n1 < 3, n2 < 4), k = k1 + 3 k2
+template <int S>
+struct Dft<12, S> {
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 y[12];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      float2 a0 = v[n2], a1 = v[4 + n2], a2 = v[8 + n2];
+      dft3<S>(a0, a1, a2);
+      y[n2 * 3 + 0] = a0;
+      y[n2 * 3 + 1] = a1;
+      y[n2 * 3 + 2] = a2;
+    }
+    // twiddles w12^{n2 k1}: w^1 = (r3, S/2), w^2 = (1/2, S r3), w^3 = S i, w^4 = (-1/2, S r3), w^6 = -1
+    y[1 * 3 + 1] = mul_cs<S>(y[4], FPM_R3, 0.5f);
+    y[1 * 3 + 2] = mul_cs<S>(y[5], 0.5f, FPM_R3);
+    y[2 * 3 + 1] = mul_cs<S>(y[7], 0.5f, FPM_R3);
+    y[2 * 3 + 2] = mul_cs<S>(y[8], -0.5f, FPM_R3);
+    y[3 * 3 + 1] = mul_si<S>(y[10]);
+    y[3 * 3 + 2] = make_float2(-y[11].x, -y[11].y);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      float2 a0 = y[k1], a1 = y[3 + k1], a2 = y[6 + k1], a3 = y[9 + k1];
+      dft4<S>(a0, a1, a2, a3);
+      v[k1] = a0;
+      v[k1 + 3] = a1;
+      v[k1 + 6] = a2;
+      v[k1 + 9] = a3;
+    }
+  }
+};
+
+}  // namespace fpm

@@ -1,0 +1,71 @@
+// Internal declarations shared by the host-side translation units of libfpm.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fpm.h"
+
+namespace fpm {
+
+// Set the calling thread's error text and return `code`.
+int fail(int code, const char *fmt, ...);
+void clear_error();
+
+struct DeviceState;   // device-side buffers of a plan (runtime.cu)
+
+// Wave-step work lists of a plan's schedule, flattened for launches.
+struct StepLists {
+  // item = (tile, led, slot, seq) ; items of step w are items[step_off[w] .. step_off[w+1])
+  std::vector<int32_t> items;       // 4 ints per item
+  std::vector<int64_t> step_off;    // [n_steps + 1]
+  // merges of step w: (tile, n_slots) pairs in merge[merge_off[w] .. merge_off[w+1])
+  std::vector<int32_t> merges;      // 2 ints per entry
+  std::vector<int64_t> merge_off;   // [n_steps + 1]
+  int32_t n_steps = 0;
+  int32_t iters = 0;                // prefix of the sequence these lists cover
+};
+
+}  // namespace fpm
+
+struct fpm_plan {
+  // problem statement (copied)
+  int32_t sensor_h = 0, sensor_w = 0, m = 0, overlap = 0, tiles_y = 0, tiles_x = 0;
+  int32_t upsample = 0, n = 0, n_tiles = 0, n_leds = 0, iters = 0, order_kind = 0;
+  double wavelength_um = 0, na = 0, pixel_um = 0, led_height_um = 0, df = 0;
+  bool epry = false;
+  std::vector<double> led_xy, defocus;
+
+  // data-independent quantities (host, FP64 -> int / complex64)
+  std::vector<int32_t> origins;     // [T][2] (y0, x0)
+  std::vector<int32_t> shifts;      // [T][L][2] (sy, sx)
+  std::vector<int32_t> order;       // [L]
+  std::vector<int32_t> waves;       // [T][iters * L]
+  std::vector<int32_t> n_waves;     // [T]
+  std::vector<uint8_t> support;     // [m][m]
+  std::vector<int32_t> chord_lo, chord_hi;   // [m], per box row; lo > hi when empty
+  int32_t y_lo = 0, y_hi = -1;      // support rows (box coordinates)
+  int32_t support_px = 0;
+  int32_t max_waves = 0, max_width = 0;
+  int64_t total_waves = 0;
+  std::vector<float> pupil0;        // [T][m][m][2]
+
+  // launch configuration of the update kernel (chosen at plan time)
+  int32_t cluster = 1, threads = 256;
+
+  fpm::DeviceState *dev = nullptr;
+  int32_t busy = 0;                 // > 0 while a server job owns the plan
+
+  // cached step lists keyed by iteration count
+  std::vector<fpm::StepLists> step_cache;
+};
+
+namespace fpm {
+// Build (or fetch from the cache) the wave-step lists for the first `iters` loops.
+const StepLists &step_lists(fpm_plan *p, int32_t iters);
+// Free device state (runtime.cu).
+void destroy_device_state(fpm_plan *p);
+// Choose cluster size and threads for (m, support rows); returns false if nothing fits.
+bool choose_launch(int32_t m, int32_t rows, int32_t *cluster, int32_t *threads);
+}  // namespace fpm

@@ -1,0 +1,613 @@
+// Host runtime of libfpm: device state of a plan, the initial guess, the
+// reconstruction launch orchestration (plain, wave-batched, CUDA graph), the
+// state getters/setters and the forward-model simulator.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "aux_kernels.cuh"
+#include "internal.h"
+#include "runtime.h"
+#include "update.cuh"
+
+namespace fpm {
+
+#define FPM_CK(call)                                                                         \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(FPM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Update-kernel variants (tile side -> factorisation, cluster, threads)
+// ---------------------------------------------------------------------------
+
+using UpdateKernel = void (*)(UpdateArgs, long long);
+
+struct Variant {
+  int m, a, b, tpt, c, t;
+  UpdateKernel k_u16, k_f32;
+  size_t (*smem)(int rows);
+};
+
+template <class Cfg>
+static Variant make_variant() {
+  return Variant{Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, &update_kernel<Cfg, uint16_t>,
+                 &update_kernel<Cfg, float>, &Cfg::smem_bytes};
+}
+
+using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128>;
+using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128>;
+using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256>;
+using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256>;
+
+static const std::vector<Variant> &variants() {
+  static const std::vector<Variant> v = {make_variant<Cfg64>(), make_variant<Cfg128>(), make_variant<Cfg192>(),
+                                         make_variant<Cfg256>()};
+  return v;
+}
+
+static constexpr size_t kMaxSmem = 232448;   // 227 KB per CTA on sm_103a
+
+static const Variant *find_variant(int m, int rows) {
+  for (const auto &v : variants())
+    if (v.m == m && v.smem(rows) <= kMaxSmem) return &v;
+  return nullptr;
+}
+
+bool choose_launch(int32_t m, int32_t rows, int32_t *cluster, int32_t *threads) {
+  const Variant *v = find_variant(m, rows);
+  if (!v) return false;
+  *cluster = v->c;
+  *threads = v->t;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Twiddle tables (FP64 -> float)
+// ---------------------------------------------------------------------------
+
+static void twiddles_2pass(int m, int a, int b, std::vector<float2> &inv, std::vector<float2> &fwd) {
+  // inv[k1*B + b] = exp(+2 pi i b k1 / m), k1 < A, b < B
+  // fwd[k1*A + b] = exp(-2 pi i b k1 / m), k1 < B, b < A
+  inv.assign(m, make_float2(0.f, 0.f));
+  fwd.assign(m, make_float2(0.f, 0.f));
+  for (int k1 = 0; k1 < a; ++k1)
+    for (int bb = 0; bb < b; ++bb) {
+      const double ang = 2.0 * M_PI * (double)(bb * k1) / m;
+      inv[k1 * b + bb] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  for (int k1 = 0; k1 < b; ++k1)
+    for (int bb = 0; bb < a; ++bb) {
+      const double ang = -2.0 * M_PI * (double)(bb * k1) / m;
+      fwd[k1 * a + bb] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+}
+
+static std::vector<float2> twiddles_line(int len, int sign) {
+  std::vector<float2> t(len);
+  for (int j = 0; j < len; ++j) {
+    const double ang = sign * 2.0 * M_PI * (double)j / len;
+    t[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  return t;
+}
+
+static bool radices_for(int len, FftLines &f) {
+  int r = len, k = 0;
+  if (r % 3 == 0) {
+    f.radix[k++] = 3;
+    r /= 3;
+  }
+  while (r % 4 == 0 && k < kMaxRadices) {
+    f.radix[k++] = 4;
+    r /= 4;
+  }
+  if (r == 2 && k < kMaxRadices) {
+    f.radix[k++] = 2;
+    r = 1;
+  }
+  f.nrad = k;
+  return r == 1 && len <= kMaxFftLen;
+}
+
+// ---------------------------------------------------------------------------
+// Device state
+// ---------------------------------------------------------------------------
+
+struct DeviceBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct StepDev {
+  int32_t iters = 0;
+  int4 *items = nullptr;
+  int2 *merges = nullptr;
+};
+
+struct GraphKey {
+  int32_t iters, mode;
+  cudaStream_t stream;
+  bool operator<(const GraphKey &o) const {
+    return iters != o.iters ? iters < o.iters : mode != o.mode ? mode < o.mode : stream < o.stream;
+  }
+};
+
+struct DeviceState {
+  int device = -1;
+  float2 *spec = nullptr, *pup = nullptr, *dpup = nullptr;
+  float *pnorm = nullptr;
+  int2 *shifts = nullptr, *origins = nullptr, *chords = nullptr;
+  float2 *tw_inv = nullptr, *tw_fwd = nullptr;      // update kernel split
+  float2 *twl_fwd_m = nullptr;                      // line FFT tables
+  int2 *norm_all = nullptr;                         // (t, 0) for every tile
+  unsigned *err = nullptr;
+  void *stack_owned = nullptr;
+  size_t stack_owned_bytes = 0;
+  const void *stack = nullptr;
+  int32_t dtype = FPM_U16;
+  long long stride_led = 0, stride_row = 0;
+  float inv_counts = 1.f;
+  bool loaded = false;
+  const Variant *var = nullptr;
+  std::vector<StepDev> steps;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+static void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+void destroy_device_state(fpm_plan *p) {
+  DeviceState *d = p->dev;
+  if (!d) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (d->device >= 0) cudaSetDevice(d->device);
+  cudaDeviceSynchronize();
+  for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &s : d->steps) {
+    dfree(s.items);
+    dfree(s.merges);
+  }
+  for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->pnorm, (void *)d->shifts,
+                  (void *)d->origins, (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd,
+                  (void *)d->twl_fwd_m, (void *)d->norm_all, (void *)d->err, d->stack_owned})
+    dfree(q);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete d;
+  p->dev = nullptr;
+}
+
+template <class T>
+static int upload(T **dst, const void *src, size_t bytes) {
+  FPM_CK(cudaMalloc((void **)dst, bytes));
+  FPM_CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return FPM_OK;
+}
+
+static int ensure_device_state(fpm_plan *p) {
+  if (p->dev) return FPM_OK;
+  DeviceState *d = new DeviceState();
+  p->dev = d;
+  FPM_CK(cudaGetDevice(&d->device));
+  const int rows = p->y_hi - p->y_lo + 1;
+  d->var = find_variant(p->m, rows);
+  if (!d->var) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", p->m, rows);
+  const size_t T = p->n_tiles, n = p->n, m = p->m;
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d->pnorm, T * sizeof(float))) != cudaSuccess)
+    return fail(FPM_ENOMEM, "device allocation of the tile state failed: %s", cudaGetErrorString(e));
+  if (p->epry) {
+    if ((e = cudaMalloc((void **)&d->dpup, T * (size_t)p->max_width * m * m * sizeof(float2))) != cudaSuccess)
+      return fail(FPM_ENOMEM, "device allocation of the pupil corrections failed: %s", cudaGetErrorString(e));
+  }
+  std::vector<int2> sh((size_t)p->n_tiles * p->n_leds), org(p->n_tiles), ch(p->m), norm(p->n_tiles);
+  for (size_t i = 0; i < sh.size(); ++i) sh[i] = make_int2(p->shifts[i * 2], p->shifts[i * 2 + 1]);
+  for (int t = 0; t < p->n_tiles; ++t) {
+    org[t] = make_int2(p->origins[t * 2], p->origins[t * 2 + 1]);
+    norm[t] = make_int2(t, 0);
+  }
+  for (int i = 0; i < p->m; ++i) ch[i] = make_int2(p->chord_lo[i], p->chord_hi[i]);
+  int rc;
+  if ((rc = upload(&d->shifts, sh.data(), sh.size() * sizeof(int2)))) return rc;
+  if ((rc = upload(&d->origins, org.data(), org.size() * sizeof(int2)))) return rc;
+  if ((rc = upload(&d->chords, ch.data(), ch.size() * sizeof(int2)))) return rc;
+  if ((rc = upload(&d->norm_all, norm.data(), norm.size() * sizeof(int2)))) return rc;
+  std::vector<float2> ti, tf;
+  twiddles_2pass(p->m, d->var->a, d->var->b, ti, tf);
+  if ((rc = upload(&d->tw_inv, ti.data(), ti.size() * sizeof(float2)))) return rc;
+  if ((rc = upload(&d->tw_fwd, tf.data(), tf.size() * sizeof(float2)))) return rc;
+  std::vector<float2> tl = twiddles_line(p->m, -1);
+  if ((rc = upload(&d->twl_fwd_m, tl.data(), tl.size() * sizeof(float2)))) return rc;
+  FPM_CK(cudaMalloc((void **)&d->err, sizeof(unsigned)));
+  FPM_CK(cudaMemset(d->err, 0, sizeof(unsigned)));
+  const size_t smem = d->var->smem(rows);
+  FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return FPM_OK;
+}
+
+// Batched 1-D FFTs over lines of a device array.
+int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
+                     long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st) {
+  FftLines f{};
+  f.data = data;
+  f.tw = tw;
+  f.len = len;
+  f.batch_stride = batch_stride;
+  f.line_stride = line_stride;
+  f.elem_stride = elem_stride;
+  f.lines_per_batch = lines_per_batch;
+  if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
+  const int threads = std::min(256, std::max(32, len / 4));
+  for (long long done = 0; done < n_lines;) {
+    const long long chunk = std::min<long long>(n_lines - done, 1LL << 30);
+    FftLines g = f;
+    // offset the base so that line indices restart at a batch boundary
+    const long long first = done;
+    g.data = data + (first / lines_per_batch) * batch_stride + (first % lines_per_batch) * line_stride;
+    if (first % lines_per_batch != 0) return fail(FPM_EINVAL, "internal: FFT chunk not batch aligned");
+    if (sign > 0) fft_lines_kernel<1><<<(unsigned)chunk, threads, 0, st>>>(g);
+    else fft_lines_kernel<-1><<<(unsigned)chunk, threads, 0, st>>>(g);
+    done += chunk;
+  }
+  FPM_CK(cudaGetLastError());
+  return FPM_OK;
+}
+
+static unsigned grid_for(long long n, int threads) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 148LL * 64));
+}
+
+// Initial guess of every tile from its image of the first LED in the order.
+static int run_init(fpm_plan *p, cudaStream_t st) {
+  DeviceState *d = p->dev;
+  const int m = p->m, n = p->n, T = p->n_tiles;
+  float2 *tmp = nullptr;
+  FPM_CK(cudaMallocAsync((void **)&tmp, (size_t)T * m * m * sizeof(float2), st));
+  const long long tot = (long long)T * m * m;
+  const int led = p->order[0];
+  if (d->dtype == FPM_U16)
+    init_gather_kernel<uint16_t><<<grid_for(tot, 256), 256, 0, st>>>(
+        tmp, (const uint16_t *)d->stack, d->stride_led, d->stride_row, d->origins, led, m, T, d->inv_counts);
+  else
+    init_gather_kernel<float><<<grid_for(tot, 256), 256, 0, st>>>(tmp, (const float *)d->stack, d->stride_led,
+                                                                    d->stride_row, d->origins, led, m, T,
+                                                                    d->inv_counts);
+  int rc;
+  // rows then columns of every tile
+  if ((rc = launch_fft_lines(tmp, d->twl_fwd_m, m, -1, (long long)T * m, m, (long long)m * m, m, 1, st))) return rc;
+  if ((rc = launch_fft_lines(tmp, d->twl_fwd_m, m, -1, (long long)T * m, m, (long long)m * m, 1, m, st))) return rc;
+  FPM_CK(cudaMemsetAsync(d->spec, 0, (size_t)T * n * n * sizeof(float2), st));
+  const float scale = (float)((double)n / m * (double)n / m);
+  init_place_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d->spec, tmp, m, n, T, scale);
+  FPM_CK(cudaGetLastError());
+  FPM_CK(cudaFreeAsync(tmp, st));
+  // pupils and their normaliser
+  FPM_CK(cudaMemcpyAsync(d->pup, p->pupil0.data(), (size_t)T * m * m * sizeof(float2), cudaMemcpyHostToDevice, st));
+  merge_kernel<<<T, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all, d->chords, p->y_lo, p->y_hi - p->y_lo + 1,
+                                  m, p->max_width);
+  FPM_CK(cudaGetLastError());
+  return FPM_OK;
+}
+
+static const StepDev *device_steps(fpm_plan *p, int32_t iters, const StepLists &sl, int *rc) {
+  DeviceState *d = p->dev;
+  for (auto &s : d->steps)
+    if (s.iters == iters) return &s;
+  StepDev s;
+  s.iters = iters;
+  *rc = upload(&s.items, sl.items.data(), std::max<size_t>(sl.items.size(), 4) * sizeof(int32_t));
+  if (*rc) return nullptr;
+  *rc = upload(&s.merges, sl.merges.data(), std::max<size_t>(sl.merges.size(), 2) * sizeof(int32_t));
+  if (*rc) return nullptr;
+  d->steps.push_back(s);
+  return &d->steps.back();
+}
+
+static UpdateArgs make_args(fpm_plan *p, const StepDev *sd) {
+  DeviceState *d = p->dev;
+  UpdateArgs a{};
+  a.spec = d->spec;
+  a.pup = d->pup;
+  a.dpup = p->epry ? d->dpup : nullptr;
+  a.pnorm = d->pnorm;
+  a.items = sd ? sd->items : nullptr;
+  a.shifts = d->shifts;
+  a.origins = d->origins;
+  a.chords = d->chords;
+  a.tw_inv = d->tw_inv;
+  a.tw_fwd = d->tw_fwd;
+  a.stack = d->stack;
+  a.stride_led = d->stride_led;
+  a.stride_row = d->stride_row;
+  a.inv_counts = d->inv_counts;
+  a.scale = (float)((double)p->n / p->m * (double)p->n / p->m);
+  a.n = p->n;
+  a.n_leds = p->n_leds;
+  a.y_lo = p->y_lo;
+  a.rows = p->y_hi - p->y_lo + 1;
+  a.slots = p->max_width;
+  a.err = d->err;
+  return a;
+}
+
+static int launch_update(fpm_plan *p, const UpdateArgs &a, long long item0, long long count, cudaStream_t st) {
+  if (count <= 0) return FPM_OK;
+  DeviceState *d = p->dev;
+  const Variant *v = d->var;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(count * v->c), 1, 1);
+  cfg.blockDim = dim3(v->t, 1, 1);
+  cfg.dynamicSmemBytes = v->smem(a.rows);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = v->c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = v->c > 1 ? 1 : 0;
+  UpdateKernel k = d->dtype == FPM_U16 ? v->k_u16 : v->k_f32;
+  FPM_CK(cudaLaunchKernelEx(&cfg, k, a, item0));
+  return FPM_OK;
+}
+
+// Enqueue the launches of `iters` loops in the given mode.
+static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st) {
+  const StepLists &sl = step_lists(p, iters);
+  int rc = 0;
+  const StepDev *sd = device_steps(p, iters, sl, &rc);
+  if (!sd) return rc;
+  const UpdateArgs a = make_args(p, sd);
+  DeviceState *d = p->dev;
+  const int rows = p->y_hi - p->y_lo + 1;
+  if (mode == FPM_RUN_WAVES) {
+    for (int s = 0; s < sl.n_steps; ++s) {
+      const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
+      if ((rc = launch_update(p, a, i0, i1 - i0, st))) return rc;
+      if (p->epry) {
+        const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
+        if (m1 > m0)
+          merge_kernel<<<(unsigned)(m1 - m0), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + m0, d->chords,
+                                                            p->y_lo, rows, p->m, p->max_width);
+      }
+    }
+    FPM_CK(cudaGetLastError());
+    return FPM_OK;
+  }
+  if (mode == FPM_RUN_PLAIN) {
+    // one tile at a time, one LED per launch; the merges close every wave
+    for (int t = 0; t < p->n_tiles; ++t) {
+      for (int s = 0; s < sl.n_steps; ++s) {
+        const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
+        // items of step s are sorted by tile
+        const int32_t *it = sl.items.data();
+        long long lo = i0, hi = i1;
+        while (lo < hi && it[lo * 4] < t) ++lo;
+        long long e = lo;
+        while (e < hi && it[e * 4] == t) ++e;
+        if (e == lo) continue;
+        for (long long k = lo; k < e; ++k)
+          if ((rc = launch_update(p, a, k, 1, st))) return rc;
+        if (p->epry) {
+          const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
+          for (long long k = m0; k < m1; ++k)
+            if (sl.merges[k * 2] == t)
+              merge_kernel<<<1, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + k, d->chords, p->y_lo, rows,
+                                              p->m, p->max_width);
+        }
+      }
+    }
+    FPM_CK(cudaGetLastError());
+    return FPM_OK;
+  }
+  return fail(FPM_EINVAL, "unknown mode %d", mode);
+}
+
+}  // namespace fpm
+
+using fpm::fail;
+
+extern "C" {
+
+int fpm_load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
+                   int64_t stride_row, float counts_per_unit, void *stream) {
+  fpm::clear_error();
+  if (!p || !stack) return fail(FPM_EINVAL, "fpm_load_tiles: null argument");
+  if (p->busy) return fail(FPM_EBUSY, "plan is owned by a server job");
+  if (dtype != FPM_U16 && dtype != FPM_F32) return fail(FPM_EINVAL, "unknown image dtype %d", dtype);
+  if (!(counts_per_unit > 0) || !std::isfinite(counts_per_unit))
+    return fail(FPM_EINVAL, "counts_per_unit must be positive and finite");
+  const int64_t es = dtype == FPM_U16 ? 2 : 4;
+  if (stride_row < p->sensor_w || stride_led < stride_row * p->sensor_h)
+    return fail(FPM_EINVAL, "strides (%lld, %lld) smaller than the image", (long long)stride_led, (long long)stride_row);
+  if ((stride_row * es) % 16 || (stride_led * es) % 16 || ((uintptr_t)stack % 16))
+    return fail(FPM_EINVAL, "stack base, rows and LED planes must be 16-byte aligned");
+  int rc;
+  if ((rc = fpm::ensure_device_state(p))) return rc;
+  fpm::DeviceState *d = p->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)((p->n_leds - 1) * stride_led + (int64_t)(p->sensor_h - 1) * stride_row + p->sensor_w) * es;
+  if (on_device) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, stack) != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return fail(FPM_EINVAL, "on_device stack is not device memory");
+    }
+    d->stack = stack;
+  } else {
+    if (d->stack_owned_bytes < bytes) {
+      if (d->stack_owned) cudaFree(d->stack_owned);
+      d->stack_owned = nullptr;
+      d->stack_owned_bytes = 0;
+      cudaError_t e = cudaMalloc(&d->stack_owned, bytes);
+      if (e != cudaSuccess) return fail(FPM_ENOMEM, "device allocation of the image stack (%zu bytes) failed", bytes);
+      d->stack_owned_bytes = bytes;
+    }
+    FPM_CK(cudaMemcpyAsync(d->stack_owned, stack, bytes, cudaMemcpyHostToDevice, st));
+    d->stack = d->stack_owned;
+  }
+  d->dtype = dtype;
+  d->stride_led = stride_led;
+  d->stride_row = stride_row;
+  d->inv_counts = 1.0f / counts_per_unit;
+  if ((rc = fpm::run_init(p, st))) return rc;
+  d->loaded = true;
+  return FPM_OK;
+}
+
+int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
+  fpm::clear_error();
+  if (!p) return fail(FPM_EINVAL, "fpm_reconstruct: null plan");
+  if (p->busy) return fail(FPM_EBUSY, "plan is owned by a server job");
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "fpm_reconstruct before fpm_load_tiles");
+  if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
+  const int base = mode & 0xff;
+  const bool graph = (mode & FPM_RUN_GRAPH) != 0;
+  if ((mode & ~(0xff | FPM_RUN_GRAPH)) || (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT))
+    return fail(FPM_EINVAL, "unknown mode 0x%x", mode);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph);
+  if (!graph) return fpm::enqueue_reconstruct(p, iters, base, st);
+  fpm::DeviceState *d = p->dev;
+  fpm::GraphKey key{iters, base, st};
+  auto it = d->graphs.find(key);
+  if (it == d->graphs.end()) {
+    // build step lists and device copies outside the capture
+    const fpm::StepLists &sl = fpm::step_lists(p, iters);
+    int rc = 0;
+    if (!fpm::device_steps(p, iters, sl, &rc)) return rc;
+    cudaStream_t cap = st;
+    bool own = false;
+    if (cap == nullptr) {
+      FPM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+    }
+    FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    rc = fpm::enqueue_reconstruct(p, iters, base, cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (own) cudaStreamDestroy(cap);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    it = d->graphs.emplace(key, ex).first;
+  }
+  FPM_CK(cudaGraphLaunch(it->second, st));
+  return FPM_OK;
+}
+
+static int copy_out(const void *src, void *dst, size_t bytes, int32_t on_device, cudaStream_t st) {
+  FPM_CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (!on_device) FPM_CK(cudaStreamSynchronize(st));
+  return FPM_OK;
+}
+
+int fpm_get_spectrum(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void *stream) {
+  fpm::clear_error();
+  if (!p || !dst) return fail(FPM_EINVAL, "fpm_get_spectrum: null argument");
+  if (tile < 0 || tile >= p->n_tiles) return fail(FPM_EINVAL, "tile %d out of range", tile);
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
+  const size_t nn = (size_t)p->n * p->n;
+  return copy_out(p->dev->spec + (size_t)tile * nn, dst, nn * sizeof(float2), on_device, (cudaStream_t)stream);
+}
+
+int fpm_get_pupil(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void *stream) {
+  fpm::clear_error();
+  if (!p || !dst) return fail(FPM_EINVAL, "fpm_get_pupil: null argument");
+  if (tile < 0 || tile >= p->n_tiles) return fail(FPM_EINVAL, "tile %d out of range", tile);
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
+  const size_t mm = (size_t)p->m * p->m;
+  return copy_out(p->dev->pup + (size_t)tile * mm, dst, mm * sizeof(float2), on_device, (cudaStream_t)stream);
+}
+
+int fpm_set_state(fpm_plan *p, int32_t tile, const void *spectrum, const void *pupil, void *stream) {
+  fpm::clear_error();
+  if (!p) return fail(FPM_EINVAL, "fpm_set_state: null plan");
+  if (tile < 0 || tile >= p->n_tiles) return fail(FPM_EINVAL, "tile %d out of range", tile);
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "fpm_set_state before fpm_load_tiles");
+  cudaStream_t st = (cudaStream_t)stream;
+  fpm::DeviceState *d = p->dev;
+  const size_t nn = (size_t)p->n * p->n, mm = (size_t)p->m * p->m;
+  if (spectrum) FPM_CK(cudaMemcpyAsync(d->spec + tile * nn, spectrum, nn * 8, cudaMemcpyHostToDevice, st));
+  if (pupil) {
+    FPM_CK(cudaMemcpyAsync(d->pup + tile * mm, pupil, mm * 8, cudaMemcpyHostToDevice, st));
+    // recompute the normaliser of this tile
+    fpm::merge_kernel<<<1, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all + tile, d->chords, p->y_lo,
+                                         p->y_hi - p->y_lo + 1, p->m, p->max_width);
+    FPM_CK(cudaGetLastError());
+  }
+  FPM_CK(cudaStreamSynchronize(st));
+  return FPM_OK;
+}
+
+int fpm_simulate(fpm_plan *p, const void *objects, float *out, void *stream) {
+  fpm::clear_error();
+  if (!p || !objects || !out) return fail(FPM_EINVAL, "fpm_simulate: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m = p->m, n = p->n, T = p->n_tiles, L = p->n_leds;
+  std::vector<int2> sh((size_t)T * L);
+  for (size_t i = 0; i < sh.size(); ++i) sh[i] = make_int2(p->shifts[i * 2], p->shifts[i * 2 + 1]);
+  float2 *spec = nullptr, *box = nullptr, *pup = nullptr, *twn = nullptr, *twm = nullptr;
+  int2 *dsh = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void *q : {(void *)spec, (void *)box, (void *)pup, (void *)twn, (void *)twm, (void *)dsh}) fpm::dfree(q);
+  };
+  int rc = FPM_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&spec, (size_t)T * n * n * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&box, (size_t)T * m * m * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&pup, (size_t)T * m * m * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&dsh, sh.size() * sizeof(int2))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&twn, (size_t)n * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&twm, (size_t)m * 8)) != cudaSuccess) {
+      rc = fail(FPM_ENOMEM, "fpm_simulate: device allocation failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    std::vector<float2> tn = fpm::twiddles_line(n, -1), tm = fpm::twiddles_line(m, +1);
+    if (cudaMemcpy(twn, tn.data(), tn.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(twm, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dsh, sh.data(), sh.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pup, p->pupil0.data(), (size_t)T * m * m * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = fail(FPM_ECUDA, "fpm_simulate: upload failed");
+      break;
+    }
+    if (cudaMemcpyAsync(spec, objects, (size_t)T * n * n * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      rc = fail(FPM_ECUDA, "fpm_simulate: objects must be device memory");
+      break;
+    }
+    if ((rc = fpm::launch_fft_lines(spec, twn, n, -1, (long long)T * n, n, (long long)n * n, n, 1, st))) break;
+    if ((rc = fpm::launch_fft_lines(spec, twn, n, -1, (long long)T * n, n, (long long)n * n, 1, n, st))) break;
+    const long long tot = (long long)T * m * m;
+    const float inv_n2 = (float)(1.0 / ((double)n * n));
+    for (int l = 0; l < L && rc == FPM_OK; ++l) {
+      fpm::sim_crop_kernel<<<fpm::grid_for(tot, 256), 256, 0, st>>>(box, spec, pup, dsh, l, L, m, n, T);
+      if ((rc = fpm::launch_fft_lines(box, twm, m, +1, (long long)T * m, m, (long long)m * m, m, 1, st))) break;
+      if ((rc = fpm::launch_fft_lines(box, twm, m, +1, (long long)T * m, m, (long long)m * m, 1, m, st))) break;
+      fpm::sim_abs_kernel<<<fpm::grid_for(tot, 256), 256, 0, st>>>(out, box, l, L, m, T, inv_n2);
+    }
+    if (rc == FPM_OK && cudaGetLastError() != cudaSuccess) rc = fail(FPM_ECUDA, "fpm_simulate: launch failed");
+  } while (0);
+  cleanup();
+  return rc;
+}
+
+}  // extern "C"

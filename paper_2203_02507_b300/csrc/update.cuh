@@ -1,0 +1,367 @@
+// Fused per-LED update of one tile (one LED sub-aperture), on one CTA or on a
+// cluster of C CTAs that share the work through distributed shared memory.
+//
+// Per update (alternating projection, Sec. 2.1; pupil correction of EPRY):
+//   Phi  = O_box * P                  (box of m x m centred at c + s)
+//   phi~ = IDFT_m(Phi)                (unnormalised; the (m/N)^2 / m^2 factor
+//                                      cancels in phi~/|phi~|)
+//   phi' = sqrt(I) phi~/|phi~|        (sqrt(I) where phi~ = 0)
+//   Phi' = (N/m)^2 DFT_m(phi')
+//   D    = Phi' - Phi
+//   O_box += conj(P) D / max|P|^2,  dP = conj(O_box_old) D / max|O_box_old|^2
+// The box is taken in its centred order: transforming a centred spectrum as if
+// it were in natural order multiplies the spatial field by (-1)^(x+y), which
+// the amplitude step preserves and the forward transform undoes, so no shift
+// is ever applied.
+//
+// Layout of the 2-D transform (m = A * B, both factors at most 16):
+//   phase 1  rows of the support (R rows): IDFT along x  -> shared "inter" [R][m]
+//   phase 2  every column: IDFT along y, amplitude step, DFT along y, keep R rows
+//   phase 3  rows of the support: DFT along x, spectrum and pupil update
+// Rows outside the support are zero before phase 1 and unused after phase 2,
+// so only R x m values are ever stored.  Each 1-D transform of length m is run
+// by TPT lanes of one warp in two register passes (radix A and radix B) with
+// one exchange through a per-group shared scratch; phases are separated by
+// a CTA (C = 1) or cluster (C > 1) barrier.  With C > 1 the columns of "inter"
+// are split across the cluster: CTA q holds columns [q m/C, (q+1) m/C).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cstdint>
+
+#include "dft.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fpm {
+
+struct UpdateArgs {
+  float2 *spec;               // [T][N][N] centred spectra
+  const float2 *pup;          // [T][m][m] centred pupils
+  float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null
+  const float *pnorm;         // [T] max |P|^2 over the support
+  const int4 *items;          // (tile, led, slot, sequence index)
+  const int2 *shifts;         // [T][L] (sy, sx)
+  const int2 *origins;        // [T] (y0, x0) on the sensor
+  const int2 *chords;         // [m] (lo, hi) support columns per box row
+  const float2 *tw_inv;       // [m] exp(+2 pi i b k1/m) at k1*B + b
+  const float2 *tw_fwd;       // [m] exp(-2 pi i b k1/m) at k1*A + b (the B x A split)
+  const void *stack;          // images, element (l, y, x) at l*stride_led + y*stride_row + x
+  long long stride_led, stride_row;
+  float inv_counts;           // intensity = element * inv_counts
+  float scale;                // (N/m)^2
+  int n;                      // N
+  int n_leds;
+  int y_lo;                   // first support row (box coordinates)
+  int rows;                   // R
+  int slots;                  // dP slots per tile
+  unsigned *err;
+};
+
+// Swizzled position of (row i, local column p) in "inter" (row length W):
+// consecutive rows of one column and columns 16 apart within one row fall in
+// different banks.
+__device__ __forceinline__ int inter_at(int i, int p, int w) { return i * w + (p ^ ((i ^ (p >> 4)) & 15)); }
+
+template <typename Img>
+__device__ __forceinline__ float load_image(const Img *img, long long off) {
+  if constexpr (sizeof(Img) == 2) {
+    return (float)__ldg(reinterpret_cast<const unsigned short *>(img) + off);
+  } else {
+    return __ldg(reinterpret_cast<const float *>(img) + off);
+  }
+}
+
+template <int M_, int A_, int B_, int TPT_, int C_, int T_>
+struct UpdateCfg {
+  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_;
+  static constexpr int W = M / C;          // columns of "inter" held by one CTA
+  static constexpr int G = T / TPT;        // transforms in flight per CTA
+  static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
+  static constexpr int UA = (B + TPT - 1) / TPT;   // units of the radix-A passes per lane
+  static constexpr int UB = (A + TPT - 1) / TPT;   // units of the radix-B passes per lane
+  static_assert(A * B == M, "m = A * B");
+  static_assert(32 % TPT == 0 && T % 32 == 0, "groups must not straddle warps");
+  static_assert(W % 16 == 0, "inter rows are swizzled in groups of 16");
+  // shared memory in bytes for R support rows
+  static size_t smem_bytes(int rows) {
+    return ((size_t)rows * W + (size_t)G * SCR + 2 * M) * sizeof(float2) + 64 * sizeof(float);
+  }
+};
+
+// One update; all threads of all C CTAs of the cluster call this with the same item.
+template <class Cfg, typename Img>
+__device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem) {
+  constexpr int M = Cfg::M, A = Cfg::A, B = Cfg::B, TPT = Cfg::TPT, C = Cfg::C, T = Cfg::T;
+  constexpr int W = Cfg::W, G = Cfg::G, SCR = Cfg::SCR;
+  const int rows = a.rows;
+  float2 *inter = smem;
+  float2 *scratch_all = inter + (size_t)rows * W;
+  float2 *twi = scratch_all + G * SCR;
+  float2 *twf = twi + M;
+  float *red = reinterpret_cast<float *>(twf + M);
+
+  const int tid = threadIdx.x;
+  const int g = tid / TPT, tl = tid % TPT;
+  const unsigned lane = tid & 31;
+  const unsigned gmask = (TPT == 32) ? 0xffffffffu : (((1u << TPT) - 1u) << (lane & ~(unsigned)(TPT - 1)));
+  float2 *scr = scratch_all + g * SCR;
+
+  int q = 0;
+  float2 *inter_of[C];
+  if constexpr (C > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    q = (int)cl.block_rank();
+#pragma unroll
+    for (int r = 0; r < C; ++r) inter_of[r] = cl.map_shared_rank(inter, r);
+  } else {
+    inter_of[0] = inter;
+  }
+
+  const int tile = item.x, led = item.y, slot = item.z;
+  const int2 sh = a.shifts[(size_t)tile * a.n_leds + led];
+  const int n = a.n;
+  const int oy = n / 2 + sh.x - M / 2, ox = n / 2 + sh.y - M / 2;
+  float2 *spec = a.spec + (size_t)tile * n * n + (size_t)oy * n + ox;   // box origin
+  const float2 *pup = a.pup + (size_t)tile * M * M;
+  const int2 org = a.origins[tile];
+  const Img *img = reinterpret_cast<const Img *>(a.stack) + (long long)led * a.stride_led +
+                   (long long)org.x * a.stride_row + org.y;
+
+  for (int i = tid; i < M; i += T) {
+    twi[i] = a.tw_inv[i];
+    twf[i] = a.tw_fwd[i];
+  }
+  __syncthreads();
+
+  // rows of the support handled by this CTA in phases 1 and 3
+  const int rpc = (rows + C - 1) / C;
+  const int r0 = q * rpc, r1 = min(rows, r0 + rpc);
+
+  // ---- phase 1: IDFT along x of every support row -------------------------
+  float omax = 0.f;
+  for (int i = r0 + g; i < r1; i += G) {
+    const int by = a.y_lo + i;
+    const int2 ch = a.chords[by];
+    const float2 *srow = spec + (size_t)by * n;
+    const float2 *prow = pup + (size_t)by * M;
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int b = tl + u * TPT;
+      if (b < B) {
+        float2 v[A];
+#pragma unroll
+        for (int aa = 0; aa < A; ++aa) {
+          const int x = B * aa + b;
+          if (x >= ch.x && x <= ch.y) {
+            const float2 o = srow[x];
+            omax = fmaxf(omax, o.x * o.x + o.y * o.y);
+            v[aa] = cmul(o, prow[x]);
+          } else {
+            v[aa] = make_float2(0.f, 0.f);
+          }
+        }
+        Dft<A, 1>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+          const float2 w = twi[k1 * B + b];
+          scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], w);
+        }
+      }
+    }
+    __syncwarp(gmask);
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u) {
+      const int k1 = tl + u * TPT;
+      if (k1 < A) {
+        float2 v[B];
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) v[bb] = scr[bb * (A + 1) + k1];
+        Dft<B, 1>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int x = k1 + A * k2;
+          const int owner = (C > 1) ? x / W : 0;
+          const int p = (C > 1) ? x - owner * W : x;
+          inter_of[owner][inter_at(i, p, W)] = v[k2];
+        }
+      }
+    }
+    __syncwarp(gmask);
+  }
+  // EPRY normaliser: max |O_box_old|^2 over the support, over the whole cluster
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+  if (lane == 0) red[tid >> 5] = omax;
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+
+  // ---- phase 2: columns: IDFT along y, amplitude step, DFT along y ---------
+  const int y_lo = a.y_lo, y_hi = a.y_lo + rows - 1;
+  for (int c = g; c < W; c += G) {
+    const int x = q * W + c;
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int b = tl + u * TPT;
+      if (b < B) {
+        float2 v[A];
+#pragma unroll
+        for (int aa = 0; aa < A; ++aa) {
+          const int y = B * aa + b;
+          v[aa] = (y >= y_lo && y <= y_hi) ? inter[inter_at(y - y_lo, c, W)] : make_float2(0.f, 0.f);
+        }
+        Dft<A, 1>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], twi[k1 * B + b]);
+      }
+    }
+    __syncwarp(gmask);
+    float2 keep[Cfg::UB][B];
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u) {
+      const int k1 = tl + u * TPT;
+      if (k1 < A) {
+        float2 *v = keep[u];
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) v[bb] = scr[bb * (A + 1) + k1];
+        Dft<B, 1>::run(v);
+        // amplitude step at y = k1 + A k2
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+          const int y = k1 + A * k2;
+          const float meas = fmaxf(load_image<Img>(img, (long long)y * a.stride_row + x) * a.inv_counts, 0.f);
+          const float2 f = v[k2];
+          const float m2 = f.x * f.x + f.y * f.y;
+          if (m2 > 0.f) {
+            const float s = (meas > 0.f) ? meas * rsqrtf(meas * m2) : 0.f;
+            v[k2] = make_float2(f.x * s, f.y * s);
+          } else {
+            v[k2] = make_float2(sqrtf(meas), 0.f);
+          }
+        }
+        // forward DFT, first pass of the B x A split: unit b' = k1, over a' = k2
+        Dft<B, -1>::run(v);
+      }
+    }
+    __syncwarp(gmask);   // everyone has read scr
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u) {
+      const int k1 = tl + u * TPT;
+      if (k1 < A) {
+#pragma unroll
+        for (int kk = 0; kk < B; ++kk)
+          scr[k1 * (B + 1) + kk] = (kk == 0) ? keep[u][0] : cmul(keep[u][kk], twf[kk * A + k1]);
+      }
+    }
+    __syncwarp(gmask);
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int kk = tl + u * TPT;   // k1' in [0, B)
+      if (kk < B) {
+        float2 v[A];
+#pragma unroll
+        for (int bb = 0; bb < A; ++bb) v[bb] = scr[bb * (B + 1) + kk];
+        Dft<A, -1>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < A; ++k2) {
+          const int y = kk + B * k2;
+          if (y >= y_lo && y <= y_hi) inter[inter_at(y - y_lo, c, W)] = v[k2];
+        }
+      }
+    }
+    __syncwarp(gmask);
+  }
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+
+  // normalisers
+  float onorm = 0.f;
+  if (tid < 32) {
+    float v = (tid < T / 32) ? red[tid] : 0.f;
+    if constexpr (C > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      for (int r = 0; r < C; ++r)
+        if (r != q && tid < T / 32) v = fmaxf(v, cl.map_shared_rank(red, r)[tid]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (tid == 0) red[32] = v;
+  }
+  __syncthreads();
+  onorm = red[32];
+  const float inv_on = (onorm > 0.f) ? 1.f / onorm : 0.f;
+  const float inv_pn = 1.f / a.pnorm[tile];
+  float2 *dp = a.dpup ? a.dpup + ((size_t)tile * a.slots + slot) * M * M : nullptr;
+
+  // ---- phase 3: DFT along x of the support rows, then the updates ----------
+  for (int i = r0 + g; i < r1; i += G) {
+    const int by = a.y_lo + i;
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u) {
+      const int b2 = tl + u * TPT;   // b' in [0, A)
+      if (b2 < A) {
+        float2 v[B];
+#pragma unroll
+        for (int aa = 0; aa < B; ++aa) {
+          const int x = A * aa + b2;
+          const int owner = (C > 1) ? x / W : 0;
+          const int p = (C > 1) ? x - owner * W : x;
+          v[aa] = inter_of[owner][inter_at(i, p, W)];
+        }
+        Dft<B, -1>::run(v);
+#pragma unroll
+        for (int kk = 0; kk < B; ++kk) scr[b2 * (B + 1) + kk] = (kk == 0) ? v[0] : cmul(v[kk], twf[kk * A + b2]);
+      }
+    }
+    __syncwarp(gmask);
+    const int2 ch = a.chords[by];
+    float2 *srow = spec + (size_t)by * n;
+    const float2 *prow = pup + (size_t)by * M;
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int kk = tl + u * TPT;
+      if (kk < B) {
+        float2 v[A];
+#pragma unroll
+        for (int bb = 0; bb < A; ++bb) v[bb] = scr[bb * (B + 1) + kk];
+        Dft<A, -1>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < A; ++k2) {
+          const int x = kk + B * k2;
+          if (x >= ch.x && x <= ch.y) {
+            const float2 o = srow[x];
+            const float2 p = prow[x];
+            const float2 phi = cmul(o, p);
+            const float2 d = csub(cscale(v[k2], a.scale), phi);
+            const float2 pc = cmulc(d, p);        // D * conj(P)
+            srow[x] = make_float2(o.x + pc.x * inv_pn, o.y + pc.y * inv_pn);
+            if (dp) {
+              const float2 oc = cmulc(d, o);      // D * conj(O_old)
+              dp[(size_t)by * M + x] = cscale(oc, inv_on);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp(gmask);
+  }
+  // keep this CTA's shared memory alive until the cluster is done reading it
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  }
+}
+
+template <class Cfg, typename Img>
+__global__ void __launch_bounds__(Cfg::T) update_kernel(const __grid_constant__ UpdateArgs a, long long item0) {
+  extern __shared__ float4 smem_raw[];
+  const int4 item = a.items[item0 + blockIdx.x / Cfg::C];
+  run_update<Cfg, Img>(a, item, reinterpret_cast<float2 *>(smem_raw));
+}
+
+}  // namespace fpm

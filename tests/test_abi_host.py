@@ -1,0 +1,96 @@
+"""Host-only checks of the C ABI: the library loads, exports every declared
+symbol, and its FP64 planning (geometry, order, waves, pupils) matches the
+oracle bit for bit.  No GPU and no compute call is needed."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fpm_oracle as orc
+
+fpm = pytest.importorskip("paper_2203_02507_b300._fpm")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "fpm.h")).read()
+    declared = set(re.findall(r"FPM_API\s+(?:int|const char \*)\s*(fpm_\w+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    assert declared == set(fpm.EXPORTED)
+    import ctypes
+    lib = ctypes.CDLL(fpm.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _oracle_geometry(w, defocus):
+    o = w.optics
+    return orc.geometry(w.sensor, w.sensor, w.tile, w.overlap, w.tiles, w.tiles, w.upsample, o.wavelength_um,
+                        o.na, o.pixel_um, synth.led_grid(o.led_side, o.led_pitch_um), o.led_height_um, defocus)
+
+
+@pytest.mark.parametrize("name", ["tile64_plain", "fov2048_m256", "batch_m128", "batch_m192"])
+def test_geometry_and_order_match_oracle_exactly(name):
+    w = synth.WORKLOADS[name]
+    dz = synth.tile_defocus(w.n_tiles, *w.defocus_um, w.seed_offset)
+    p = fpm.plan_for(w, defocus_um=dz, iters=1)
+    s = p.schedule()
+    g = _oracle_geometry(w, dz)
+    assert np.array_equal(s["origins"], g.origins)
+    assert np.array_equal(s["shifts"], g.shifts)
+    assert np.array_equal(s["order"], g.order)
+    assert p.info["support_px"] == int(g.support.sum())
+    for t in (0, w.n_tiles - 1):
+        np.testing.assert_allclose(p.initial_pupil(t), g.pupils[t], rtol=0, atol=2e-7)
+        assert np.array_equal(p.initial_pupil(t) != 0, g.support)
+
+
+@pytest.mark.parametrize("name,iters,tiles", [("tile64_plain", 10, [0]), ("fov2048_m256", 2, [0, 27, 63]),
+                                              ("batch_m128", 3, [0, 9]), ("batch_m192", 2, [5])])
+def test_waves_match_oracle_exactly(name, iters, tiles):
+    w = synth.WORKLOADS[name]
+    dz = synth.tile_defocus(w.n_tiles, *w.defocus_um, w.seed_offset)
+    p = fpm.plan_for(w, defocus_um=dz, iters=iters)
+    s = p.schedule()
+    g = _oracle_geometry(w, dz)
+    seq = orc.sequence(g.order, iters)
+    for t in tiles:
+        ref = orc.waves(g.n, g.support, g.shifts[t], seq)
+        assert np.array_equal(s["waves"][t], ref), f"tile {t}"
+
+
+def test_wave_prefix_property():
+    """The schedule of k loops is the first k*L entries of the schedule of more loops."""
+    w = synth.WORKLOADS["fov2048_m256"]
+    a = fpm.plan_for(w, iters=3).schedule()["waves"]
+    b = fpm.plan_for(w, iters=1).schedule()["waves"]
+    assert np.array_equal(a[:, :b.shape[1]], b)
+
+
+def _desc(**kw):
+    base = dict(sensor=256, tile=64, overlap=0, tiles=1, upsample=4, wavelength_um=0.532, na=0.1,
+                pixel_um=1.625, led_xy_um=synth.led_grid(5, 4000.0), led_height_um=90000.0, iters=1)
+    base.update(kw)
+    return base
+
+
+@pytest.mark.parametrize("bad", [dict(tile=100), dict(upsample=1), dict(overlap=64), dict(tiles=5),
+                                 dict(na=0.0), dict(na=1.5), dict(iters=0), dict(led_height_um=-1.0),
+                                 dict(upsample=2, led_xy_um=synth.led_grid(15, 4000.0) * 3)])
+def test_invalid_descriptions_are_rejected(bad):
+    with pytest.raises(fpm.FpmError) as e:
+        fpm.Plan(**_desc(**bad))
+    assert e.value.code == fpm.EINVAL
+    assert str(e.value)
+
+
+def test_device_calls_before_load_fail_cleanly():
+    p = fpm.Plan(**_desc())
+    with pytest.raises(fpm.FpmError) as e:
+        p.reconstruct(1)
+    assert e.value.code == fpm.ESTATE
+    with pytest.raises(fpm.FpmError):
+        p.spectrum(0)
+    p.close()
