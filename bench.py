@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the FPM tile-reconstruction hot path on B300.
+
+A step is one full-FOV reconstruction: the initial guess of every tile
+(fpm_load_tiles) plus all iteration loops of the per-LED update with the wave
+schedule (fpm_reconstruct, replayed as a CUDA graph).  The headline workload is
+the 2048 x 2048 sensor cut into 8 x 8 tiles of 256 x 256 (HR 1024 x 1024),
+15 x 15 LEDs, 20 loops with EPRY pupil correction: 288,000 LED sub-aperture
+updates per step.  Inputs (1.9 GB image stack, 0.5 GB spectra) are larger than
+L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "LED sub-aperture updates/sec and ms per FOV; p50/p99 job latency vs plain path"
+UNIT = "updates/s"
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
+
+EXTRA = {
+    # small case of the same kernel for ncu captures: 3 x 3 tiles of 256, inputs > L2
+    "ncu_m256": synth.Workload("ncu_m256", sensor=768, tile=256, tiles=3, overlap=16, iters=1, epry=True,
+                               optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
+}
+
+
+def workload(name):
+    return synth.WORKLOADS.get(name) or EXTRA[name]
+
+
+def support_px(w):
+    m, o = w.tile, w.optics
+    df = 1.0 / (m * o.pixel_um)
+    k = np.arange(m) - m // 2
+    fy, fx = np.meshgrid(k * df, k * df, indexing="ij")
+    return int((np.sqrt(fx * fx + fy * fy) <= o.na / o.wavelength_um).sum())
+
+
+def flops_per_update(w):
+    """Algorithmic FLOPs of one update: two m x m 2-D FFTs at 5 n log2 n (n = m^2),
+    10 flop per pixel for the amplitude step, and 18 (fixed pupil) or 36 (EPRY)
+    flop per support pixel for the box products and the corrections."""
+    m = w.tile
+    a = support_px(w)
+    return 2 * 5 * m * m * math.log2(m * m) + 10 * m * m + (36 if w.epry else 18) * a
+
+
+def bytes_per_update(w):
+    """Algorithmic HBM bytes of one update: the LR image once, the spectrum's
+    support disc read and written (16 B/px), the pupil disc read (8 B/px) and,
+    with EPRY, its correction written (8 B/px)."""
+    m = w.tile
+    a = support_px(w)
+    img = 2 if w.image_dtype == "u16" else 4
+    return img * m * m + 16 * a + (16 if w.epry else 8) * a
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# synthetic data on the device
+# ---------------------------------------------------------------------------
+
+def device_stack(plan, w, torch, dev):
+    """Sensor stack [L, S, S] of 12-bit counts (int16 bits) simulated on the GPU."""
+    t_n, n, m, l_n = w.n_tiles, w.hr, w.tile, w.n_leds
+    objs = torch.empty((t_n, n, n), dtype=torch.complex64, device=dev)
+    for t in range(t_n):
+        objs[t].copy_(torch.from_numpy(synth.hr_object(n, t, w.seed_offset).astype(np.complex64)))
+    imgs = torch.empty((t_n, l_n, m, m), dtype=torch.float32, device=dev)
+    plan.simulate(objs, imgs)
+    del objs
+    if w.image_dtype == "f32":
+        stack = torch.zeros((l_n, w.sensor, w.sensor), dtype=torch.float32, device=dev)
+        k = 1.0
+        counts = imgs
+    else:
+        g = torch.Generator(device=dev).manual_seed(synth.SEED_NOISE + w.seed_offset)
+        k = float(w.peak_counts / imgs.max().item())
+        counts = torch.poisson(imgs * k, generator=g)
+        counts += torch.randn(counts.shape, generator=g, device=dev) * w.read_sigma
+        counts = counts.round_().clamp_(0, 4095).to(torch.int16)
+        stack = torch.zeros((l_n, w.sensor, w.sensor), dtype=torch.int16, device=dev)
+    origins = plan.schedule()["origins"]
+    win = synth.owner_windows(origins, m, w.sensor)
+    for t in range(t_n):
+        y0, x0 = (int(v) for v in origins[t])
+        ylo, yhi, xlo, xhi = (int(v) for v in win[t])
+        stack[:, y0 + ylo:y0 + yhi, x0 + xlo:x0 + xhi] = counts[t, :, ylo:yhi, xlo:xhi]
+    del imgs, counts
+    torch.cuda.synchronize()
+    return stack, k
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure; only this leg of bench.py uses it)
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    name, tile, iters = args
+    from oracle import fpm_oracle as orc
+    if iters == 0:                      # pool warm-up: imports only
+        return 0.0, 0
+    w = workload(name)
+    o = w.optics
+    leds = synth.led_grid(o.led_side, o.led_pitch_um)
+    dz = synth.tile_defocus(w.n_tiles, *w.defocus_um, w.seed_offset)
+    g = orc.geometry(w.sensor, w.sensor, w.tile, w.overlap, w.tiles, w.tiles, w.upsample, o.wavelength_um, o.na,
+                     o.pixel_um, leds, o.led_height_um, dz)
+    imgs = orc.forward_images(orc.fft2c(synth.hr_object(w.hr, tile, w.seed_offset)), g.pupils[tile],
+                              g.shifts[tile], w.tile)
+    t0 = time.perf_counter()
+    orc.reconstruct_tile(imgs, g.shifts[tile], g.order, g.support, g.pupils[tile], g.n, iters, w.epry)
+    return time.perf_counter() - t0, iters * w.n_leds
+
+
+def cpu_baseline(name, tiles=1, iters=1, procs=1):
+    """Oracle updates/s on host cores: `procs` processes, one tile each (the paper's
+    one-sub-region-per-CPU strategy), `iters` loops."""
+    jobs = [(name, t, iters) for t in range(tiles)]
+    if procs == 1:
+        res = [_oracle_worker(j) for j in jobs]
+        wall = sum(r[0] for r in res)
+    else:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(procs) as pool:
+            pool.map(_oracle_worker, [(name, 0, 0)] * procs)          # import warm-up
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    upd = sum(r[1] for r in res)
+    return upd / wall, upd, wall
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    procs = max(1, min(os.cpu_count() or 1, w.n_tiles, 32))
+    times, ups = [], 0
+    for s in range(args.warmup + args.steps):
+        v, upd, wall = cpu_baseline(args.workload, tiles=procs, iters=1, procs=procs)
+        if s >= args.warmup:
+            times.append(wall)
+            ups = upd
+    value = ups / statistics.mean(times)
+    sample = f"{procs} tiles x 1 loop ({ups} updates) per step, one process per tile"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.updates / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sensor": w.sensor, "tile": w.tile, "tiles": w.n_tiles,
+                       "leds": w.n_leds, "iters": w.iters, "epry": w.epry},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fov2048_m256")
+    ap.add_argument("--mode", default="waves", choices=["waves", "persistent"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2203_02507_b300 import plan_for
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+
+    plan = plan_for(w)
+    stack, k = device_stack(plan, w, torch, dev)
+    stream = torch.cuda.current_stream()
+
+    def step(timed=False):
+        plan.load_tiles(stack, k)
+        plan.reconstruct(w.iters, mode=args.mode, graph=True, timed=timed and args.mode == "waves")
+
+    for _ in range(max(args.warmup, 1)):
+        step(timed=True)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(timed=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = plan.stats()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * w.updates / (ms_per_step / 1e3)
+    launches = (st["load_launches"] + st["run_launches"]) * args.steps
+
+    # roofline of the fused update kernel from the event-timed launches of the last step
+    fpu, bpu = flops_per_update(w), bytes_per_update(w)
+    roof = None
+    if st["update_ms"] > 0:
+        per_launch_s = st["update_ms"] / 1e3 / st["update_launches"]
+        upl = st["updates"] / st["update_launches"]
+        achieved = fpu * upl / per_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "fpm::update_kernel", "launches_per_step": st["update_launches"],
+                "updates_per_launch": upl, "avg_launch_us": per_launch_s * 1e6,
+                "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
+                "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9,
+                "update_kernel_share": st["update_ms"] / ms_per_step,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (max SM clock)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "sensor": w.sensor, "tile": w.tile, "hr": w.hr, "tiles": w.n_tiles,
+                       "leds": w.n_leds, "iters": w.iters, "epry": w.epry, "updates_per_step": w.updates,
+                       "mode": args.mode + "+graph", "ms_per_fov": ms_per_step,
+                       "l2": "inputs larger than L2 (1.9 GB stack, 0.5 GB spectra); no flush",
+                       "parallelism": f"{world} independent FOV replicas" if world > 1 else "1 GPU"},
+            "roofline": roof, "gpu_launches": launches, "clocks": clk}
+
+    if not args.no_extras and rank == 0:
+        # e2e through the public API with host buffers: H2D of the stack, D2H of every spectrum
+        host_stack = torch.empty(stack.shape, dtype=stack.dtype, pin_memory=True)
+        host_stack.copy_(stack)
+        host_out = torch.empty((w.n_tiles, w.hr, w.hr), dtype=torch.complex64, pin_memory=True)
+        plan.load_tiles(host_stack, k)
+        plan.reconstruct(w.iters, mode=args.mode, graph=True)
+        torch.cuda.synchronize()
+        k_e2e = max(2, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            plan.load_tiles(host_stack, k)
+            plan.reconstruct(w.iters, mode=args.mode, graph=True)
+            for t in range(w.n_tiles):
+                plan.spectrum(t, out=host_out[t])
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / k_e2e
+        line["e2e"] = {"value": w.updates / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": int(host_stack.numel() * host_stack.element_size()),
+                       "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()),
+                       "ms_per_step": e2e_s * 1e3, "steps": k_e2e}
+        # plain path: one tile at a time, one LED per launch (bounded: one loop)
+        plan.load_tiles(stack, k)
+        plan.reconstruct(1, mode="waves")          # builds the one-loop schedule lists
+        plan.load_tiles(stack, k)
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        plan.reconstruct(1, mode="plain")
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - p0
+        plain_upd = w.n_tiles * w.n_leds
+        line["plain_path"] = {"value": plain_upd / plain_s, "unit": UNIT,
+                              "sample": f"one loop of all {w.n_tiles} tiles ({plain_upd} updates), no graph",
+                              "speedup_of_batched": value / (plain_upd / plain_s)}
+        if world == 1:
+            v, upd, wall = cpu_baseline(w.name, tiles=1, iters=4, procs=1)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"1 tile x 4 loops ({upd} updates, {wall:.1f} s), FP64 numpy"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

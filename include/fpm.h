@@ -74,6 +74,8 @@ extern "C" {
 #define FPM_RUN_WAVES      1  /* every tile's next wave in one launch            */
 #define FPM_RUN_PERSISTENT 2  /* one persistent kernel over a device work queue  */
 #define FPM_RUN_GRAPH      0x100 /* OR-able: replay the launches as a CUDA graph */
+#define FPM_RUN_TIMED      0x200 /* OR-able with FPM_RUN_WAVES: time each update
+                                    launch with CUDA events (see fpm_get_stats)  */
 
 typedef struct fpm_plan fpm_plan;
 typedef struct fpm_server fpm_server;
@@ -187,8 +189,8 @@ FPM_API int fpm_load_tiles(fpm_plan *plan, const void *stack, int32_t dtype, int
  * Maxima run over the pupil support.  Updates of one wave use the pupil as it
  * was when the wave started; their pupil corrections are added in sequence
  * order when the wave ends.  `mode` is FPM_RUN_PLAIN, FPM_RUN_WAVES or
- * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH; all modes give the same
- * result.  FPM_ESTATE before fpm_load_tiles; FPM_ETIMEOUT if a bounded device
+ * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH (and, with FPM_RUN_WAVES,
+ * | FPM_RUN_TIMED); all modes give the same result.  FPM_ESTATE before fpm_load_tiles; FPM_ETIMEOUT if a bounded device
  * wait of the persistent kernel gave up (the state is then undefined).
  */
 FPM_API int fpm_reconstruct(fpm_plan *plan, int32_t iters, int32_t mode, void *stream);
@@ -209,6 +211,20 @@ FPM_API int fpm_get_pupil(fpm_plan *plan, int32_t tile, void *dst, int32_t on_de
  */
 FPM_API int fpm_set_state(fpm_plan *plan, int32_t tile, const void *spectrum, const void *pupil,
                   void *stream);
+
+/* Counters of the last calls on a plan (see fpm_get_stats). */
+typedef struct {
+  int64_t load_launches;    /* kernels enqueued by the last fpm_load_tiles             */
+  int64_t run_launches;     /* kernels enqueued by the last fpm_reconstruct (a graph
+                               replay counts the kernel nodes it runs)                 */
+  int64_t update_launches;  /* fused-update launches of the last FPM_RUN_TIMED run     */
+  int64_t updates;          /* LED updates those launches performed                    */
+  double update_ms;         /* summed device time of those launches, milliseconds      */
+} fpm_stats;
+
+/* fpm_get_stats -- fill *out.  Waits for the events of the last FPM_RUN_TIMED
+ * run (if any) to complete; update_ms is 0 when no timed run happened. */
+FPM_API int fpm_get_stats(fpm_plan *plan, fpm_stats *out);
 
 /* fpm_initial_pupil -- the plan's initial pupil of `tile` (host memory,
  * m x m centred complex64; host only, no CUDA call). */

@@ -23,6 +23,7 @@ EPRY = 1
 U16, F32 = 0, 1
 RUN = {"plain": 0, "waves": 1, "persistent": 2}
 RUN_GRAPH = 0x100
+RUN_TIMED = 0x200
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 
@@ -58,6 +59,14 @@ class PlanInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Stats(C.Structure):
+    _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
+                ("updates", C.c_int64), ("update_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp, _i32, _i64, _f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
 _SIGS = {
     "fpm_plan_create": [C.POINTER(PlanDesc), C.POINTER(_vp)],
@@ -70,6 +79,7 @@ _SIGS = {
     "fpm_get_pupil": [_vp, _i32, _vp, _i32, _vp],
     "fpm_set_state": [_vp, _i32, _vp, _vp, _vp],
     "fpm_initial_pupil": [_vp, _i32, _vp],
+    "fpm_get_stats": [_vp, C.POINTER(Stats)],
     "fpm_simulate": [_vp, _vp, _vp, _vp],
     "fpm_server_create": [C.c_size_t, C.POINTER(_vp)],
     "fpm_submit": [_vp, _vp, _i32, C.POINTER(_i64)],
@@ -189,9 +199,15 @@ class Plan:
                                    float(counts_per_unit), _stream(stream)))
         self._stack_ref = stack if on_dev else None   # borrowed device memory stays alive
 
-    def reconstruct(self, iters: int | None = None, mode: str = "waves", graph: bool = False, stream=None):
-        flag = RUN[mode] | (RUN_GRAPH if graph else 0)
+    def reconstruct(self, iters: int | None = None, mode: str = "waves", graph: bool = False, timed: bool = False,
+                    stream=None):
+        flag = RUN[mode] | (RUN_GRAPH if graph else 0) | (RUN_TIMED if timed else 0)
         _check(_lib.fpm_reconstruct(self._h, int(iters or self.iters), flag, _stream(stream)))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(_lib.fpm_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
 
     def spectrum(self, tile: int, out=None, stream=None):
         if out is None:

@@ -158,6 +158,13 @@ struct DeviceState {
   const Variant *var = nullptr;
   std::vector<StepDev> steps;
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, int64_t> graph_launches;
+  // counters (fpm_get_stats)
+  int64_t load_launches = 0, run_launches = 0;
+  std::vector<cudaEvent_t> events;            // 2 per wave step of a timed run
+  std::vector<int64_t> timed_steps;           // steps whose update launch was timed
+  int64_t timed_updates = 0;
+  bool timed_valid = false;
 };
 
 static void dfree(void *p) {
@@ -172,6 +179,7 @@ void destroy_device_state(fpm_plan *p) {
   if (d->device >= 0) cudaSetDevice(d->device);
   cudaDeviceSynchronize();
   for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
+  for (cudaEvent_t ev : d->events) cudaEventDestroy(ev);
   for (auto &s : d->steps) {
     dfree(s.items);
     dfree(s.merges);
@@ -297,6 +305,7 @@ static int run_init(fpm_plan *p, cudaStream_t st) {
   merge_kernel<<<T, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all, d->chords, p->y_lo, p->y_hi - p->y_lo + 1,
                                   m, p->max_width);
   FPM_CK(cudaGetLastError());
+  d->load_launches = 5;   // gather, 2 x line FFT, place, normaliser
   return FPM_OK;
 }
 
@@ -362,8 +371,10 @@ static int launch_update(fpm_plan *p, const UpdateArgs &a, long long item0, long
   return FPM_OK;
 }
 
-// Enqueue the launches of `iters` loops in the given mode.
-static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st) {
+// Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
+// With `timed`, CUDA events bracket every update launch (waves mode only).
+static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st, bool timed, bool capturing,
+                               int64_t *launches) {
   const StepLists &sl = step_lists(p, iters);
   int rc = 0;
   const StepDev *sd = device_steps(p, iters, sl, &rc);
@@ -371,18 +382,43 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
   const UpdateArgs a = make_args(p, sd);
   DeviceState *d = p->dev;
   const int rows = p->y_hi - p->y_lo + 1;
+  int64_t nl = 0;
   if (mode == FPM_RUN_WAVES) {
+    if (timed) {
+      while ((int)d->events.size() < 2 * sl.n_steps) {
+        cudaEvent_t ev;
+        FPM_CK(cudaEventCreate(&ev));
+        d->events.push_back(ev);
+      }
+      d->timed_steps.clear();
+      d->timed_updates = 0;
+      d->timed_valid = true;
+    }
     for (int s = 0; s < sl.n_steps; ++s) {
       const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
+      if (timed && i1 > i0) {
+        FPM_CK(capturing ? cudaEventRecordWithFlags(d->events[2 * s], st, cudaEventRecordExternal)
+                         : cudaEventRecord(d->events[2 * s], st));
+      }
       if ((rc = launch_update(p, a, i0, i1 - i0, st))) return rc;
+      if (i1 > i0) ++nl;
+      if (timed && i1 > i0) {
+        FPM_CK(capturing ? cudaEventRecordWithFlags(d->events[2 * s + 1], st, cudaEventRecordExternal)
+                         : cudaEventRecord(d->events[2 * s + 1], st));
+        d->timed_steps.push_back(s);
+        d->timed_updates += i1 - i0;
+      }
       if (p->epry) {
         const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
-        if (m1 > m0)
+        if (m1 > m0) {
           merge_kernel<<<(unsigned)(m1 - m0), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + m0, d->chords,
                                                             p->y_lo, rows, p->m, p->max_width);
+          ++nl;
+        }
       }
     }
     FPM_CK(cudaGetLastError());
+    *launches = nl;
     return FPM_OK;
   }
   if (mode == FPM_RUN_PLAIN) {
@@ -397,21 +433,47 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
         long long e = lo;
         while (e < hi && it[e * 4] == t) ++e;
         if (e == lo) continue;
-        for (long long k = lo; k < e; ++k)
+        for (long long k = lo; k < e; ++k) {
           if ((rc = launch_update(p, a, k, 1, st))) return rc;
+          ++nl;
+        }
         if (p->epry) {
           const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
           for (long long k = m0; k < m1; ++k)
-            if (sl.merges[k * 2] == t)
+            if (sl.merges[k * 2] == t) {
               merge_kernel<<<1, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + k, d->chords, p->y_lo, rows,
                                               p->m, p->max_width);
+              ++nl;
+            }
         }
       }
     }
     FPM_CK(cudaGetLastError());
+    *launches = nl;
     return FPM_OK;
   }
   return fail(FPM_EINVAL, "unknown mode %d", mode);
+}
+
+int get_stats(fpm_plan *p, fpm_stats *out) {
+  std::memset(out, 0, sizeof(*out));
+  DeviceState *d = p->dev;
+  if (!d) return FPM_OK;
+  out->load_launches = d->load_launches;
+  out->run_launches = d->run_launches;
+  if (d->timed_valid && !d->timed_steps.empty()) {
+    FPM_CK(cudaEventSynchronize(d->events[2 * d->timed_steps.back() + 1]));
+    double ms = 0;
+    for (int64_t s : d->timed_steps) {
+      float f = 0.f;
+      FPM_CK(cudaEventElapsedTime(&f, d->events[2 * s], d->events[2 * s + 1]));
+      ms += f;
+    }
+    out->update_ms = ms;
+    out->update_launches = (int64_t)d->timed_steps.size();
+    out->updates = d->timed_updates;
+  }
+  return FPM_OK;
 }
 
 }  // namespace fpm
@@ -474,13 +536,21 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
   const int base = mode & 0xff;
   const bool graph = (mode & FPM_RUN_GRAPH) != 0;
-  if ((mode & ~(0xff | FPM_RUN_GRAPH)) || (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT))
+  const bool timed = (mode & FPM_RUN_TIMED) != 0;
+  if ((mode & ~(0xff | FPM_RUN_GRAPH | FPM_RUN_TIMED)) ||
+      (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT))
     return fail(FPM_EINVAL, "unknown mode 0x%x", mode);
+  if (timed && base != FPM_RUN_WAVES) return fail(FPM_EINVAL, "FPM_RUN_TIMED needs FPM_RUN_WAVES");
   cudaStream_t st = (cudaStream_t)stream;
-  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph);
-  if (!graph) return fpm::enqueue_reconstruct(p, iters, base, st);
   fpm::DeviceState *d = p->dev;
-  fpm::GraphKey key{iters, base, st};
+  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph);
+  if (!graph) {
+    int64_t nl = 0;
+    int rc = fpm::enqueue_reconstruct(p, iters, base, st, timed, false, &nl);
+    d->run_launches = nl;
+    return rc;
+  }
+  fpm::GraphKey key{iters, mode & 0xfff, st};
   auto it = d->graphs.find(key);
   if (it == d->graphs.end()) {
     // build step lists and device copies outside the capture
@@ -494,7 +564,9 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
       own = true;
     }
     FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    rc = fpm::enqueue_reconstruct(p, iters, base, cap);
+    int64_t nl = 0;
+    rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
+    d->graph_launches[key] = nl;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (own) cudaStreamDestroy(cap);
@@ -509,8 +581,26 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     if (e != cudaSuccess) return fail(FPM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     it = d->graphs.emplace(key, ex).first;
   }
+  if (timed) {
+    // the events of this graph belong to its capture-time schedule
+    const fpm::StepLists &sl = fpm::step_lists(p, iters);
+    d->timed_steps.clear();
+    d->timed_updates = 0;
+    for (int s = 0; s < sl.n_steps; ++s)
+      if (sl.step_off[s + 1] > sl.step_off[s]) {
+        d->timed_steps.push_back(s);
+        d->timed_updates += sl.step_off[s + 1] - sl.step_off[s];
+      }
+    d->timed_valid = true;
+  }
   FPM_CK(cudaGraphLaunch(it->second, st));
+  d->run_launches = d->graph_launches[key];
   return FPM_OK;
+}
+
+int fpm_get_stats(fpm_plan *p, fpm_stats *out) {
+  if (!p || !out) return fail(FPM_EINVAL, "fpm_get_stats: null argument");
+  return fpm::get_stats(p, out);
 }
 
 static int copy_out(const void *src, void *dst, size_t bytes, int32_t on_device, cudaStream_t st) {

