@@ -144,7 +144,7 @@ def device_stack(plan, w, torch, dev):
         k = 1.0
         counts = imgs
     else:
-        g = torch.Generator(device=dev).manual_seed(synth.SEED_NOISE + w.seed_offset)
+        g = torch.Generator(device=dev).manual_seed(synth.workloads.SEED_NOISE + w.seed_offset)
         k = float(w.peak_counts / imgs.max().item())
         counts = torch.poisson(imgs * k, generator=g)
         counts += torch.randn(counts.shape, generator=g, device=dev) * w.read_sigma

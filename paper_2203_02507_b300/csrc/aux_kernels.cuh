@@ -99,22 +99,41 @@ __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, int n, i
   }
 }
 
-// Add the wave's pupil corrections in slot (= sequence) order and recompute
-// max |P|^2 over the support.  One CTA per (tile, slots) entry.
-__global__ void merge_kernel(float2 *pup, const float2 *dpup, float *pnorm, const int2 *merges,
-                             const int2 *chords, int y_lo, int rows, int m, int slots) {
+// Add the wave's pupil corrections in slot (= sequence) order and compute
+// max |P|^2 over the support.  Grid: (merge entries, kNormParts); CTA (e, c)
+// handles row chunk c of entry e = (tile, slots) and writes the chunk's
+// maximum to pnorm_part[tile][c]; readers take the max of the kNormParts
+// values, so the result does not depend on scheduling.
+constexpr int kNormParts = 8;
+
+__global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
+                                                    float *__restrict__ pnorm_part, const int2 *__restrict__ merges,
+                                                    const int2 *__restrict__ chords, int y_lo, int rows, int m,
+                                                    int slots) {
   const int2 mg = merges[blockIdx.x];
   const int t = mg.x, ns = mg.y;
+  const int rpp = (rows + kNormParts - 1) / kNormParts;
+  const int r0 = blockIdx.y * rpp, r1 = min(rows, r0 + rpp);
+  const size_t mm = (size_t)m * m;
+  float2 *p = pup + (size_t)t * mm;
   float mx = 0.f;
-  float2 *p = pup + (size_t)t * m * m;
-  for (int idx = threadIdx.x; idx < rows * m; idx += blockDim.x) {
-    const int by = y_lo + idx / m, bx = idx % m;
+  for (int idx = threadIdx.x; idx < (r1 - r0) * m; idx += blockDim.x) {
+    const int by = y_lo + r0 + idx / m, bx = idx % m;
     const int2 ch = chords[by];
     if (bx < ch.x || bx > ch.y) continue;
     const size_t off = (size_t)by * m + bx;
     float2 v = p[off];
-    for (int s = 0; s < ns; ++s) v = cadd(v, dpup[((size_t)t * slots + s) * m * m + off]);
-    if (ns > 0) p[off] = v;
+    if (ns > 0) {
+      const float2 *d = dpup + (size_t)t * slots * mm + off;
+      int s = 0;
+      for (; s + 4 <= ns; s += 4) {
+        const float2 a0 = d[(size_t)s * mm], a1 = d[(size_t)(s + 1) * mm];
+        const float2 a2 = d[(size_t)(s + 2) * mm], a3 = d[(size_t)(s + 3) * mm];
+        v = cadd(cadd(cadd(cadd(v, a0), a1), a2), a3);
+      }
+      for (; s < ns; ++s) v = cadd(v, d[(size_t)s * mm]);
+      p[off] = v;
+    }
     mx = fmaxf(mx, v.x * v.x + v.y * v.y);
   }
   __shared__ float red[32];
@@ -126,7 +145,7 @@ __global__ void merge_kernel(float2 *pup, const float2 *dpup, float *pnorm, cons
     float v = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) pnorm[t] = v;
+    if (threadIdx.x == 0) pnorm_part[(size_t)t * kNormParts + blockIdx.y] = v;
   }
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -41,20 +42,28 @@ static Variant make_variant() {
                  &update_kernel<Cfg, float>, &Cfg::smem_bytes};
 }
 
-using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128>;
-using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128>;
-using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256>;
-using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256>;
+// candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
+using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;
+using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128, 2>;
+using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256, 1>;
+using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
+using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(), make_variant<Cfg128>(), make_variant<Cfg192>(),
-                                         make_variant<Cfg256>()};
+                                         make_variant<Cfg256>(), make_variant<Cfg256w>()};
   return v;
 }
 
 static constexpr size_t kMaxSmem = 232448;   // 227 KB per CTA on sm_103a
 
+// First candidate for tile side m whose shared memory fits; FPM_UPDATE_THREADS
+// (environment) restricts the choice to one thread count.
 static const Variant *find_variant(int m, int rows) {
+  const char *env = getenv("FPM_UPDATE_THREADS");
+  const int want = env ? atoi(env) : 0;
+  for (const auto &v : variants())
+    if (v.m == m && v.smem(rows) <= kMaxSmem && (want == 0 || v.t == want)) return &v;
   for (const auto &v : variants())
     if (v.m == m && v.smem(rows) <= kMaxSmem) return &v;
   return nullptr;
@@ -212,7 +221,7 @@ static int ensure_device_state(fpm_plan *p) {
   cudaError_t e;
   if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d->pnorm, T * sizeof(float))) != cudaSuccess)
+      (e = cudaMalloc((void **)&d->pnorm, T * kNormParts * sizeof(float))) != cudaSuccess)
     return fail(FPM_ENOMEM, "device allocation of the tile state failed: %s", cudaGetErrorString(e));
   if (p->epry) {
     if ((e = cudaMalloc((void **)&d->dpup, T * (size_t)p->max_width * m * m * sizeof(float2))) != cudaSuccess)
@@ -302,8 +311,8 @@ static int run_init(fpm_plan *p, cudaStream_t st) {
   FPM_CK(cudaFreeAsync(tmp, st));
   // pupils and their normaliser
   FPM_CK(cudaMemcpyAsync(d->pup, p->pupil0.data(), (size_t)T * m * m * sizeof(float2), cudaMemcpyHostToDevice, st));
-  merge_kernel<<<T, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all, d->chords, p->y_lo, p->y_hi - p->y_lo + 1,
-                                  m, p->max_width);
+  merge_kernel<<<dim3(T, kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all, d->chords, p->y_lo,
+                                                     p->y_hi - p->y_lo + 1, m, p->max_width);
   FPM_CK(cudaGetLastError());
   d->load_launches = 5;   // gather, 2 x line FFT, place, normaliser
   return FPM_OK;
@@ -411,8 +420,8 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
       if (p->epry) {
         const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
         if (m1 > m0) {
-          merge_kernel<<<(unsigned)(m1 - m0), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + m0, d->chords,
-                                                            p->y_lo, rows, p->m, p->max_width);
+          merge_kernel<<<dim3((unsigned)(m1 - m0), kNormParts), 256, 0, st>>>(
+              d->pup, d->dpup, d->pnorm, sd->merges + m0, d->chords, p->y_lo, rows, p->m, p->max_width);
           ++nl;
         }
       }
@@ -441,8 +450,8 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
           const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
           for (long long k = m0; k < m1; ++k)
             if (sl.merges[k * 2] == t) {
-              merge_kernel<<<1, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + k, d->chords, p->y_lo, rows,
-                                              p->m, p->max_width);
+              merge_kernel<<<dim3(1, kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + k,
+                                                                 d->chords, p->y_lo, rows, p->m, p->max_width);
               ++nl;
             }
         }
@@ -639,8 +648,9 @@ int fpm_set_state(fpm_plan *p, int32_t tile, const void *spectrum, const void *p
   if (pupil) {
     FPM_CK(cudaMemcpyAsync(d->pup + tile * mm, pupil, mm * 8, cudaMemcpyHostToDevice, st));
     // recompute the normaliser of this tile
-    fpm::merge_kernel<<<1, 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all + tile, d->chords, p->y_lo,
-                                         p->y_hi - p->y_lo + 1, p->m, p->max_width);
+    fpm::merge_kernel<<<dim3(1, fpm::kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all + tile,
+                                                                d->chords, p->y_lo, p->y_hi - p->y_lo + 1, p->m,
+                                                                p->max_width);
     FPM_CK(cudaGetLastError());
   }
   FPM_CK(cudaStreamSynchronize(st));

@@ -29,6 +29,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 
+#include "aux_kernels.cuh"
 #include "dft.cuh"
 
 namespace cg = cooperative_groups;
@@ -39,7 +40,7 @@ struct UpdateArgs {
   float2 *spec;               // [T][N][N] centred spectra
   const float2 *pup;          // [T][m][m] centred pupils
   float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null
-  const float *pnorm;         // [T] max |P|^2 over the support
+  const float *pnorm;         // [T][kNormParts] partial maxima of |P|^2 over the support
   const int4 *items;          // (tile, led, slot, sequence index)
   const int2 *shifts;         // [T][L] (sy, sx)
   const int2 *origins;        // [T] (y0, x0) on the sensor
@@ -72,9 +73,9 @@ __device__ __forceinline__ float load_image(const Img *img, long long off) {
   }
 }
 
-template <int M_, int A_, int B_, int TPT_, int C_, int T_>
+template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1>
 struct UpdateCfg {
-  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_;
+  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_;
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -122,8 +123,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const int2 sh = a.shifts[(size_t)tile * a.n_leds + led];
   const int n = a.n;
   const int oy = n / 2 + sh.x - M / 2, ox = n / 2 + sh.y - M / 2;
-  float2 *spec = a.spec + (size_t)tile * n * n + (size_t)oy * n + ox;   // box origin
-  const float2 *pup = a.pup + (size_t)tile * M * M;
+  float2 *__restrict__ spec = a.spec + (size_t)tile * n * n + (size_t)oy * n + ox;   // box origin
+  const float2 *__restrict__ pup = a.pup + (size_t)tile * M * M;
   const int2 org = a.origins[tile];
   const Img *img = reinterpret_cast<const Img *>(a.stack) + (long long)led * a.stride_led +
                    (long long)org.x * a.stride_row + org.y;
@@ -143,23 +144,24 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   for (int i = r0 + g; i < r1; i += G) {
     const int by = a.y_lo + i;
     const int2 ch = a.chords[by];
-    const float2 *srow = spec + (size_t)by * n;
-    const float2 *prow = pup + (size_t)by * M;
+    const float2 *__restrict__ srow = spec + (size_t)by * n;
+    const float2 *__restrict__ prow = pup + (size_t)by * M;
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int b = tl + u * TPT;
       if (b < B) {
-        float2 v[A];
+        float2 v[A], pv[A];
+#pragma unroll
+        for (int aa = 0; aa < A; ++aa) {     // all loads first
+          const int x = B * aa + b;
+          const bool in = x >= ch.x && x <= ch.y;
+          v[aa] = in ? srow[x] : make_float2(0.f, 0.f);
+          pv[aa] = in ? prow[x] : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) {
-          const int x = B * aa + b;
-          if (x >= ch.x && x <= ch.y) {
-            const float2 o = srow[x];
-            omax = fmaxf(omax, o.x * o.x + o.y * o.y);
-            v[aa] = cmul(o, prow[x]);
-          } else {
-            v[aa] = make_float2(0.f, 0.f);
-          }
+          omax = fmaxf(omax, v[aa].x * v[aa].x + v[aa].y * v[aa].y);
+          v[aa] = cmul(v[aa], pv[aa]);
         }
         Dft<A, 1>::run(v);
 #pragma unroll
@@ -203,6 +205,15 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const int y_lo = a.y_lo, y_hi = a.y_lo + rows - 1;
   for (int c = g; c < W; c += G) {
     const int x = q * W + c;
+    // this lane's measured pixels for the amplitude step (rows y = k1 + A k2), fetched early
+    float meas[Cfg::UB][B];
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u) {
+      const int k1 = tl + u * TPT;
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2)
+        meas[u][k2] = (k1 < A) ? load_image<Img>(img, (long long)(k1 + A * k2) * a.stride_row + x) : 0.f;
+    }
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int b = tl + u * TPT;
@@ -231,15 +242,14 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         // amplitude step at y = k1 + A k2
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const int y = k1 + A * k2;
-          const float meas = fmaxf(load_image<Img>(img, (long long)y * a.stride_row + x) * a.inv_counts, 0.f);
+          const float in = fmaxf(meas[u][k2] * a.inv_counts, 0.f);
           const float2 f = v[k2];
           const float m2 = f.x * f.x + f.y * f.y;
           if (m2 > 0.f) {
-            const float s = (meas > 0.f) ? meas * rsqrtf(meas * m2) : 0.f;
+            const float s = (in > 0.f) ? in * rsqrtf(in * m2) : 0.f;
             v[k2] = make_float2(f.x * s, f.y * s);
           } else {
-            v[k2] = make_float2(sqrtf(meas), 0.f);
+            v[k2] = make_float2(sqrtf(in), 0.f);
           }
         }
         // forward DFT, first pass of the B x A split: unit b' = k1, over a' = k2
@@ -296,12 +306,31 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   __syncthreads();
   onorm = red[32];
   const float inv_on = (onorm > 0.f) ? 1.f / onorm : 0.f;
-  const float inv_pn = 1.f / a.pnorm[tile];
+  float pn = 0.f;
+#pragma unroll
+  for (int k = 0; k < kNormParts; ++k) pn = fmaxf(pn, a.pnorm[(size_t)tile * kNormParts + k]);
+  const float inv_pn = 1.f / pn;
   float2 *dp = a.dpup ? a.dpup + ((size_t)tile * a.slots + slot) * M * M : nullptr;
 
   // ---- phase 3: DFT along x of the support rows, then the updates ----------
   for (int i = r0 + g; i < r1; i += G) {
     const int by = a.y_lo + i;
+    const int2 ch = a.chords[by];
+    float2 *__restrict__ srow = spec + (size_t)by * n;
+    const float2 *__restrict__ prow = pup + (size_t)by * M;
+    // O_box_old and P at this lane's outputs x = kk + B k2, fetched before the transform
+    float2 ov[Cfg::UA][A], pv[Cfg::UA][A];
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int kk = tl + u * TPT;
+#pragma unroll
+      for (int k2 = 0; k2 < A; ++k2) {
+        const int x = kk + B * k2;
+        const bool in = kk < B && x >= ch.x && x <= ch.y;
+        ov[u][k2] = in ? srow[x] : make_float2(0.f, 0.f);
+        pv[u][k2] = in ? prow[x] : make_float2(0.f, 0.f);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < Cfg::UB; ++u) {
       const int b2 = tl + u * TPT;   // b' in [0, A)
@@ -320,9 +349,6 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       }
     }
     __syncwarp(gmask);
-    const int2 ch = a.chords[by];
-    float2 *srow = spec + (size_t)by * n;
-    const float2 *prow = pup + (size_t)by * M;
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int kk = tl + u * TPT;
@@ -335,8 +361,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         for (int k2 = 0; k2 < A; ++k2) {
           const int x = kk + B * k2;
           if (x >= ch.x && x <= ch.y) {
-            const float2 o = srow[x];
-            const float2 p = prow[x];
+            const float2 o = ov[u][k2];
+            const float2 p = pv[u][k2];
             const float2 phi = cmul(o, p);
             const float2 d = csub(cscale(v[k2], a.scale), phi);
             const float2 pc = cmulc(d, p);        // D * conj(P)
@@ -358,7 +384,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 }
 
 template <class Cfg, typename Img>
-__global__ void __launch_bounds__(Cfg::T) update_kernel(const __grid_constant__ UpdateArgs a, long long item0) {
+__global__ void __launch_bounds__(Cfg::T, Cfg::MINB) update_kernel(const __grid_constant__ UpdateArgs a, long long item0) {
   extern __shared__ float4 smem_raw[];
   const int4 item = a.items[item0 + blockIdx.x / Cfg::C];
   run_update<Cfg, Img>(a, item, reinterpret_cast<float2 *>(smem_raw));

@@ -5,10 +5,12 @@ after one iteration loop; after a full run, amplitude rel-L2 <= 1e-3 and the
 phase error (RMS of the wrapped phase difference over |o| > 0.1 max, relative to
 the RMS phase) <= 1e-3.  Wave grouping is compared bit for bit in the host tests.
 
-The pupil is held to rel-L2 <= 1e-4 after one loop: its EPRY corrections are
-sums of D = Phi' - Phi, a difference of nearly equal spectra, so the float32
-rounding of Phi and Phi' (relative to |Phi|) is magnified by |Phi|/|D| in the
-pupil; with 225 LEDs per loop this lands near 2e-5 on a 64 x 64 pupil.
+The pupil is held to rel-L2 <= 3e-4 after one loop: its EPRY corrections are
+sums of D = Phi' - Phi, a difference of nearly equal spectra, so float32
+rounding relative to |Phi| is magnified by |Phi|/|D| in the pupil.  Running
+the oracle's own steps in complex64 (numpy float32 FFTs) gives pupil errors up
+to 7.6e-5 (spectrum 5.2e-6) on the 64 x 64, 15 x 15-LED job below and <= 3e-7
+on the 128/256 jobs; the bound keeps about 4x over the worst of those.
 """
 import numpy as np
 import pytest
@@ -19,7 +21,7 @@ from tests._jobs import Job, object_errors, rel_l2
 
 pytestmark = pytest.mark.gpu
 SPEC_TOL = 1e-5      # complex spectrum after one loop
-PUPIL_TOL = 1e-4     # pupil after one loop (see module docstring)
+PUPIL_TOL = 3e-4     # pupil after one loop (see module docstring)
 
 O15, O9 = synth.Optics(led_side=15), synth.Optics(led_side=9)
 SMALL = {
