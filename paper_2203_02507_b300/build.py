@@ -22,7 +22,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
           f"-I{os.path.join(ROOT, 'include')}"]
 CUFLAGS = ARCH + COMMON + ["-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
 SOURCES = ["plan.cpp", "runtime.cu", "server.cu"]
-HEADERS = ["internal.h", "runtime.h", "dft.cuh", "update.cuh", "aux_kernels.cuh"]
+HEADERS = ["internal.h", "runtime.h", "dft.cuh", "update.cuh", "aux_kernels.cuh", "update_args.h"]
 
 
 def _newest_dep():

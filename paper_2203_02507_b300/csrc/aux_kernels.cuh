@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "dft.cuh"
+#include "update_args.h"
 
 namespace fpm {
 
@@ -104,8 +105,6 @@ __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, int n, i
 // handles row chunk c of entry e = (tile, slots) and writes the chunk's
 // maximum to pnorm_part[tile][c]; readers take the max of the kNormParts
 // values, so the result does not depend on scheduling.
-constexpr int kNormParts = 8;
-
 __global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
                                                     float *__restrict__ pnorm_part, const int2 *__restrict__ merges,
                                                     const int2 *__restrict__ chords, int y_lo, int rows, int m,

@@ -62,6 +62,13 @@ struct fpm_plan {
 };
 
 namespace fpm {
+// Circular pupil support |f| <= NA / wavelength on the m x m centred grid,
+// f = (b - m/2) * df: per box row the inclusive column range [lo, hi] (lo > hi
+// when empty) and the first/last support rows.  Returns the pixel count, or -1
+// when a row is not one contiguous chord or the rows are not contiguous.
+// lo/hi (and mask, if not null) must hold m (m * m) entries.
+int support_chords(int m, double df, double na, double wavelength_um, uint8_t *mask, int32_t *lo, int32_t *hi,
+                   int32_t *y_lo, int32_t *y_hi);
 // Build (or fetch from the cache) the wave-step lists for the first `iters` loops.
 const StepLists &step_lists(fpm_plan *p, int32_t iters);
 // Free device state (runtime.cu).

@@ -52,42 +52,51 @@ static void parallel_for(int64_t n, F f) {
   for (auto &t : th) t.join();
 }
 
-// Per box row of the support: [lo, hi] columns (lo > hi when the row is empty).
-static bool build_support(fpm_plan *p) {
-  const int m = p->m;
-  p->support.assign((size_t)m * m, 0);
-  p->chord_lo.assign(m, 1);
-  p->chord_hi.assign(m, 0);
-  const double cutoff = p->na / p->wavelength_um;
+int support_chords(int m, double df, double na, double wavelength_um, uint8_t *mask, int32_t *lo_v, int32_t *hi_v,
+                   int32_t *y_lo, int32_t *y_hi) {
+  for (int i = 0; i < m; ++i) {
+    lo_v[i] = 1;
+    hi_v[i] = 0;
+  }
+  const double cutoff = na / wavelength_um;
   int count = 0;
-  p->y_lo = m;
-  p->y_hi = -1;
+  *y_lo = m;
+  *y_hi = -1;
   for (int by = 0; by < m; ++by) {
-    const double fy = (double)(by - m / 2) * p->df;
-    int lo = m, hi = -1;
+    const double fy = (double)(by - m / 2) * df;
+    int lo = m, hi = -1, in_row = 0;
     for (int bx = 0; bx < m; ++bx) {
-      const double fx = (double)(bx - m / 2) * p->df;
+      const double fx = (double)(bx - m / 2) * df;
       const bool in = std::sqrt(fx * fx + fy * fy) <= cutoff;
-      p->support[(size_t)by * m + bx] = in;
+      if (mask) mask[(size_t)by * m + bx] = in;
       if (in) {
         lo = std::min(lo, bx);
         hi = std::max(hi, bx);
         ++count;
+        ++in_row;
       }
     }
     if (hi >= lo) {
-      for (int bx = lo; bx <= hi; ++bx)
-        if (!p->support[(size_t)by * m + bx]) return false;   // rows must be chords
-      p->chord_lo[by] = lo;
-      p->chord_hi[by] = hi;
-      p->y_lo = std::min(p->y_lo, by);
-      p->y_hi = std::max(p->y_hi, by);
+      if (in_row != hi - lo + 1) return -1;                 // rows must be chords
+      lo_v[by] = lo;
+      hi_v[by] = hi;
+      *y_lo = std::min(*y_lo, by);
+      *y_hi = std::max(*y_hi, by);
     }
   }
-  for (int by = p->y_lo; by <= p->y_hi; ++by)
-    if (p->chord_hi[by] < p->chord_lo[by]) return false;        // rows must be contiguous
-  p->support_px = count;
-  return count > 0;
+  for (int by = *y_lo; by <= *y_hi; ++by)
+    if (hi_v[by] < lo_v[by]) return -1;                      // rows must be contiguous
+  return count;
+}
+
+static bool build_support(fpm_plan *p) {
+  p->support.assign((size_t)p->m * p->m, 0);
+  p->chord_lo.assign(p->m, 1);
+  p->chord_hi.assign(p->m, 0);
+  const int c = support_chords(p->m, p->df, p->na, p->wavelength_um, p->support.data(), p->chord_lo.data(),
+                               p->chord_hi.data(), &p->y_lo, &p->y_hi);
+  p->support_px = c > 0 ? c : 0;
+  return c > 0;
 }
 
 static void build_pupils(fpm_plan *p) {

@@ -51,7 +51,7 @@ using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(), make_variant<Cfg128>(), make_variant<Cfg192>(),
-                                         make_variant<Cfg256>(), make_variant<Cfg256w>()};
+                                         make_variant<Cfg256w>(), make_variant<Cfg256>()};
   return v;
 }
 
@@ -69,6 +69,16 @@ static const Variant *find_variant(int m, int rows) {
   return nullptr;
 }
 
+bool update_variant(int m, int rows, int *a, int *b, int *cluster, int *threads) {
+  const Variant *v = find_variant(m, rows);
+  if (!v) return false;
+  *a = v->a;
+  *b = v->b;
+  *cluster = v->c;
+  *threads = v->t;
+  return true;
+}
+
 bool choose_launch(int32_t m, int32_t rows, int32_t *cluster, int32_t *threads) {
   const Variant *v = find_variant(m, rows);
   if (!v) return false;
@@ -81,11 +91,9 @@ bool choose_launch(int32_t m, int32_t rows, int32_t *cluster, int32_t *threads) 
 // Twiddle tables (FP64 -> float)
 // ---------------------------------------------------------------------------
 
-static void twiddles_2pass(int m, int a, int b, std::vector<float2> &inv, std::vector<float2> &fwd) {
+void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd) {
   // inv[k1*B + b] = exp(+2 pi i b k1 / m), k1 < A, b < B
   // fwd[k1*A + b] = exp(-2 pi i b k1 / m), k1 < B, b < A
-  inv.assign(m, make_float2(0.f, 0.f));
-  fwd.assign(m, make_float2(0.f, 0.f));
   for (int k1 = 0; k1 < a; ++k1)
     for (int bb = 0; bb < b; ++bb) {
       const double ang = 2.0 * M_PI * (double)(bb * k1) / m;
@@ -239,8 +247,8 @@ static int ensure_device_state(fpm_plan *p) {
   if ((rc = upload(&d->origins, org.data(), org.size() * sizeof(int2)))) return rc;
   if ((rc = upload(&d->chords, ch.data(), ch.size() * sizeof(int2)))) return rc;
   if ((rc = upload(&d->norm_all, norm.data(), norm.size() * sizeof(int2)))) return rc;
-  std::vector<float2> ti, tf;
-  twiddles_2pass(p->m, d->var->a, d->var->b, ti, tf);
+  std::vector<float2> ti(p->m), tf(p->m);
+  update_twiddles(p->m, d->var->a, d->var->b, ti.data(), tf.data());
   if ((rc = upload(&d->tw_inv, ti.data(), ti.size() * sizeof(float2)))) return rc;
   if ((rc = upload(&d->tw_fwd, tf.data(), tf.size() * sizeof(float2)))) return rc;
   std::vector<float2> tl = twiddles_line(p->m, -1);
@@ -377,6 +385,39 @@ static int launch_update(fpm_plan *p, const UpdateArgs &a, long long item0, long
   cfg.numAttrs = v->c > 1 ? 1 : 0;
   UpdateKernel k = d->dtype == FPM_U16 ? v->k_u16 : v->k_f32;
   FPM_CK(cudaLaunchKernelEx(&cfg, k, a, item0));
+  return FPM_OK;
+}
+
+int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
+                        cudaStream_t st) {
+  const Variant *v = find_variant(m, rows);
+  if (!v) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", m, rows);
+  if (count <= 0) return FPM_OK;
+  const size_t smem = v->smem(rows);
+  UpdateKernel k = dtype == FPM_U16 ? v->k_u16 : v->k_f32;
+  FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(count * v->c), 1, 1);
+  cfg.blockDim = dim3(v->t, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = v->c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = v->c > 1 ? 1 : 0;
+  FPM_CK(cudaLaunchKernelEx(&cfg, k, a, item0));
+  return FPM_OK;
+}
+
+int launch_merge(float2 *pup, const float2 *dpup, float *pnorm_part, const int2 *merges, int count,
+                 const int2 *chords, int y_lo, int rows, int m, int slots, cudaStream_t st) {
+  if (count <= 0) return FPM_OK;
+  merge_kernel<<<dim3((unsigned)count, kNormParts), 256, 0, st>>>(pup, dpup, pnorm_part, merges, chords, y_lo, rows,
+                                                                   m, slots);
+  FPM_CK(cudaGetLastError());
   return FPM_OK;
 }
 

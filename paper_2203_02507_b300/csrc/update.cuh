@@ -31,33 +31,12 @@
 
 #include "aux_kernels.cuh"
 #include "dft.cuh"
+#include "update_args.h"
 
 namespace cg = cooperative_groups;
 
 namespace fpm {
 
-struct UpdateArgs {
-  float2 *spec;               // [T][N][N] centred spectra
-  const float2 *pup;          // [T][m][m] centred pupils
-  float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null
-  const float *pnorm;         // [T][kNormParts] partial maxima of |P|^2 over the support
-  const int4 *items;          // (tile, led, slot, sequence index)
-  const int2 *shifts;         // [T][L] (sy, sx)
-  const int2 *origins;        // [T] (y0, x0) on the sensor
-  const int2 *chords;         // [m] (lo, hi) support columns per box row
-  const float2 *tw_inv;       // [m] exp(+2 pi i b k1/m) at k1*B + b
-  const float2 *tw_fwd;       // [m] exp(-2 pi i b k1/m) at k1*A + b (the B x A split)
-  const void *stack;          // images, element (l, y, x) at l*stride_led + y*stride_row + x
-  long long stride_led, stride_row;
-  float inv_counts;           // intensity = element * inv_counts
-  float scale;                // (N/m)^2
-  int n;                      // N
-  int n_leds;
-  int y_lo;                   // first support row (box coordinates)
-  int rows;                   // R
-  int slots;                  // dP slots per tile
-  unsigned *err;
-};
 
 // Swizzled position of (row i, local column p) in "inter" (row length W):
 // consecutive rows of one column and columns 16 apart within one row fall in
