@@ -266,6 +266,34 @@ FPM_API int fpm_poll(fpm_server *server, fpm_job job, int32_t *state, double *wa
 /* fpm_server_destroy -- finish or cancel queued jobs, stop the server, free it. */
 FPM_API int fpm_server_destroy(fpm_server *server);
 
+/*
+ * fpm_update_tile_static -- one LED update of one tile, allocating no device
+ * memory.  The paper has no counterpart: it exists for callers that cannot
+ * call cudaMalloc (a host whose device memory belongs to its own pool, a
+ * plug-in that may not allocate after start-up, or a real-time acquisition
+ * loop that an allocation and its implicit synchronisation would stall).
+ *   spectrum  device, n x n centred complex64, updated in place
+ *   pupil     device, m x m centred complex64 (zero outside the circular
+ *             support |f| <= na/wavelength), corrected in place if epry != 0
+ *   image     device, m x m float32 measured intensity of this LED, model units
+ *   shift_y, shift_x  the LED's sub-aperture shift in Fourier pixels (as
+ *             fpm_get_schedule reports it)
+ *   m in {64, 128, 192, 256}; n = 2..8 times m.
+ * It computes exactly what fpm_reconstruct computes for a wave holding this one
+ * LED: the max |P|^2 normaliser of the current pupil, the spectrum update and,
+ * with epry, the pupil correction added.  Every temporary lives in a fixed
+ * 1 MiB array of static device memory that each device loading the library
+ * holds until the process exits; sizes needing more are rejected with
+ * FPM_EINVAL.  All calls on a device share that array, so calls that overlap
+ * on the GPU (other streams, unordered host threads) race; calls on one
+ * stream are ordered.  The first call on each device looks up the array's
+ * address (and sets the kernels' shared-memory limit), so make it before
+ * any timing-critical loop.  Stream-ordered; the caller synchronises.
+ */
+FPM_API int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32_t m, const float *image,
+                                   int32_t shift_y, int32_t shift_x, double wavelength_um, double na,
+                                   double pixel_um, int32_t epry, void *stream);
+
 /* fpm_last_error -- text of the calling thread's last failure ("" if none). */
 FPM_API const char *fpm_last_error(void);
 

@@ -85,6 +85,7 @@ _SIGS = {
     "fpm_submit": [_vp, _vp, _i32, C.POINTER(_i64)],
     "fpm_poll": [_vp, _i64, C.POINTER(_i32), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "fpm_server_destroy": [_vp],
+    "fpm_update_tile_static": [_vp, _i32, _vp, _i32, _vp, _i32, _i32, C.c_double, C.c_double, C.c_double, _i32, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -271,6 +272,19 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def update_tile_static(spectrum, pupil, image, shift, wavelength_um, na, pixel_um, epry, stream=None):
+    """One LED update of one tile with no device allocation (fpm_update_tile_static).
+
+    spectrum: device complex64 [N, N]; pupil: device complex64 [m, m]; image:
+    device float32 [m, m]; shift: (sy, sx).  Updates spectrum (and pupil if
+    epry) in place, stream-ordered.
+    """
+    n, m = int(spectrum.shape[-1]), int(pupil.shape[-1])
+    _check(_lib.fpm_update_tile_static(_ptr(spectrum), n, _ptr(pupil), m, _ptr(image), int(shift[0]),
+                                       int(shift[1]), float(wavelength_um), float(na), float(pixel_um),
+                                       1 if epry else 0, _stream(stream)))
 
 
 def plan_for(workload, defocus_um=None, iters=None) -> Plan:

@@ -1,0 +1,172 @@
+// One LED update of one tile that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: a host whose device memory is entirely
+// reserved by its own pool allocator, a plug-in that may not allocate after
+// start-up, or a real-time acquisition loop in which an allocation (and the
+// device synchronisation that cudaMalloc/cudaFree can imply) would stall the
+// camera.  fpm_update_tile_static serves them: the caller passes the spectrum,
+// the pupil and the measured image, and every temporary the update needs (the
+// pupil correction, the normaliser partials, the support chords, the twiddle
+// tables and the one-item work list) lives in the file-scope array below.
+//
+// The array is a fixed 1 MiB per device that loads this library, held until
+// the process exits.  All calls on a device share it and it keeps the last
+// call's contents; every byte a call reads is first written by that same call
+// (nothing has to start at zero), and calls that overlap on the GPU (different
+// streams, or different host threads without ordering) race on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+#include "runtime.h"
+
+namespace fpm {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;
+
+static __device__ __align__(256) unsigned char g_fpm_static_scratch[kStaticScratchBytes];
+
+// Host side: the array's device address, looked up once per device.
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static void *g_scratch_addr[kMaxDevices] = {};
+
+static int scratch_address(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(FPM_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fpm_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(FPM_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return FPM_OK;
+}
+
+static bool is_device_pointer(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace fpm
+
+using fpm::fail;
+
+extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32_t m, const float *image,
+                                      int32_t shift_y, int32_t shift_x, double wavelength_um, double na,
+                                      double pixel_um, int32_t epry, void *stream) {
+  fpm::clear_error();
+  if (!spectrum || !pupil || !image) return fail(FPM_EINVAL, "fpm_update_tile_static: null argument");
+  if (m < 16 || m > 4096 || m % 16) return fail(FPM_EINVAL, "tile side %d out of range", m);
+  if (n < 2 * m || n > 8 * m || n % m)
+    return fail(FPM_EINVAL, "HR side %d must be 2..8 times the tile side %d", n, m);
+  // layout of the static array: [pupil correction m*m][partial maxima][tables]
+  const size_t dp_bytes = (size_t)m * m * sizeof(float2);
+  const size_t norm_off = fpm::align256(dp_bytes);
+  const size_t blob_off = norm_off + 256;
+  const size_t chords_b = (size_t)m * sizeof(int2), tw_b = (size_t)m * sizeof(float2);
+  const size_t blob_bytes = chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + 2 * sizeof(int2);
+  const size_t need = blob_off + blob_bytes;
+  if (need > fpm::kStaticScratchBytes)
+    return fail(FPM_EINVAL, "tile side %d needs %zu bytes of static scratch; the limit is %zu", m, need,
+                fpm::kStaticScratchBytes);
+  if (m != 64 && m != 128 && m != 192 && m != 256)
+    return fail(FPM_EINVAL, "tile side %d not supported (64, 128, 192 or 256)", m);
+  if (!(wavelength_um > 0) || !(na > 0) || !(na < 1) || !(pixel_um > 0))
+    return fail(FPM_EINVAL, "optics must be positive (0 < NA < 1)");
+  const int64_t oy = n / 2 + (int64_t)shift_y - m / 2, ox = n / 2 + (int64_t)shift_x - m / 2;
+  if (oy < 0 || ox < 0 || oy + m > n || ox + m > n)
+    return fail(FPM_EINVAL, "shift (%d, %d) moves the %d x %d box out of the %d x %d spectrum", shift_y, shift_x, m,
+                m, n, n);
+  if (!fpm::is_device_pointer(spectrum) || !fpm::is_device_pointer(pupil) || !fpm::is_device_pointer(image))
+    return fail(FPM_EINVAL, "spectrum, pupil and image must be device memory");
+
+  // support chords, FP64, exactly as the plan computes them
+  int32_t lo[256], hi[256], y_lo = 0, y_hi = -1;
+  const double df = 1.0 / (m * pixel_um);
+  if (fpm::support_chords(m, df, na, wavelength_um, nullptr, lo, hi, &y_lo, &y_hi) <= 0)
+    return fail(FPM_EINVAL, "pupil support is empty or not a disc");
+  const int rows = y_hi - y_lo + 1;
+  int fa = 0, fb = 0, fc = 0, ft = 0;
+  if (!fpm::update_variant(m, rows, &fa, &fb, &fc, &ft))
+    return fail(FPM_EINVAL, "pupil support (%d rows) too large for tile %d", rows, m);
+
+  void *base = nullptr;
+  int rc = fpm::scratch_address(&base);
+  if (rc) return rc;
+  unsigned char *dev = static_cast<unsigned char *>(base);
+
+  // tables, built on the stack and copied with one stream-ordered copy
+  alignas(16) unsigned char blob[256 * 8 + 2 * 256 * 8 + 64];
+  unsigned char *w = blob;
+  int2 *ch = reinterpret_cast<int2 *>(w);
+  for (int i = 0; i < m; ++i) ch[i] = make_int2(lo[i], hi[i]);
+  w += chords_b;
+  float2 *twi = reinterpret_cast<float2 *>(w);
+  float2 *twf = twi + m;
+  fpm::update_twiddles(m, fa, fb, twi, twf);
+  w += 2 * tw_b;
+  int4 *item = reinterpret_cast<int4 *>(w);
+  *item = make_int4(0, 0, 0, 0);
+  int2 *sh = reinterpret_cast<int2 *>(item + 1);
+  sh[0] = make_int2(shift_y, shift_x);   // shift of LED 0
+  sh[1] = make_int2(0, 0);               // origin of tile 0 in the image
+  int2 *mg = sh + 2;
+  mg[0] = make_int2(0, 0);               // normaliser only
+  mg[1] = make_int2(0, 1);               // add one correction, then normaliser
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dev + blob_off, blob, blob_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "copy of the update tables: %s", cudaGetErrorString(e));
+
+  const int2 *d_chords = reinterpret_cast<const int2 *>(dev + blob_off);
+  const float2 *d_twi = reinterpret_cast<const float2 *>(dev + blob_off + chords_b);
+  const float2 *d_twf = d_twi + m;
+  const int4 *d_item = reinterpret_cast<const int4 *>(dev + blob_off + chords_b + 2 * tw_b);
+  const int2 *d_sh = reinterpret_cast<const int2 *>(d_item + 1);
+  const int2 *d_mg = d_sh + 2;
+  float2 *d_dp = reinterpret_cast<float2 *>(dev);
+  float *d_norm = reinterpret_cast<float *>(dev + norm_off);
+  float2 *pup = static_cast<float2 *>(pupil);
+
+  // 1. max |P|^2 of the current pupil  2. the update  3. (EPRY) add its correction
+  if ((rc = fpm::launch_merge(pup, d_dp, d_norm, d_mg, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
+  fpm::UpdateArgs a{};
+  a.spec = static_cast<float2 *>(spectrum);
+  a.pup = pup;
+  a.dpup = epry ? d_dp : nullptr;
+  a.pnorm = d_norm;
+  a.items = d_item;
+  a.shifts = d_sh;
+  a.origins = d_sh + 1;
+  a.chords = d_chords;
+  a.tw_inv = d_twi;
+  a.tw_fwd = d_twf;
+  a.stack = image;
+  a.stride_led = (long long)m * m;
+  a.stride_row = m;
+  a.inv_counts = 1.f;
+  a.scale = (float)((double)n / m * (double)n / m);
+  a.n = n;
+  a.n_leds = 1;
+  a.y_lo = y_lo;
+  a.rows = rows;
+  a.slots = 1;
+  a.err = nullptr;
+  if ((rc = fpm::launch_update_items(m, rows, FPM_F32, a, 0, 1, st))) return rc;
+  if (epry && (rc = fpm::launch_merge(pup, d_dp, d_norm, d_mg + 1, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
+  return FPM_OK;
+}
