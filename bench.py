@@ -37,6 +37,12 @@ UNIT = "updates/s"
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
 
+# DRAM bytes per update of the fused update kernel (m = 256, EPRY), from the ncu
+# capture summarised in profiles/update_kernel_m256_ncu_full.md: 4,285,696 B read
+# and 0 B written for a launch of 9 updates.  A full launch scales it by its
+# updates.  Set to None whenever the kernel changes until it is re-captured.
+TRAFFIC_PER_UPDATE = {256: 4285696 / 9}
+
 EXTRA = {
     # small case of the same kernel for ncu captures: 3 x 3 tiles of 256, inputs > L2
     "ncu_m256": synth.Workload("ncu_m256", sensor=768, tile=256, tiles=3, overlap=16, iters=1, epry=True,
@@ -304,7 +310,10 @@ def main():
         upl = st["updates"] / st["update_launches"]
         achieved = fpu * upl / per_launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": (TRAFFIC_PER_UPDATE[w.tile] * upl if w.tile in TRAFFIC_PER_UPDATE else None),
+                "traffic_source": "ncu dram__bytes_read+write of a 9-update launch (3x3 tiles of 256), "
+                                  "scaled to the average launch's updates",
                 "kernel": "fpm::update_kernel", "launches_per_step": st["update_launches"],
                 "updates_per_launch": upl, "avg_launch_us": per_launch_s * 1e6,
                 "flop_per_update": fpu, "hbm_bytes_per_update": bpu,

@@ -76,6 +76,13 @@ extern "C" {
 #define FPM_RUN_GRAPH      0x100 /* OR-able: replay the launches as a CUDA graph */
 #define FPM_RUN_TIMED      0x200 /* OR-able with FPM_RUN_WAVES: time each update
                                     launch with CUDA events (see fpm_get_stats)  */
+#define FPM_RUN_FAULT_TEST 0x400 /* OR-able with FPM_RUN_PERSISTENT, for tests of
+                                    the failure path only: every dependency wait
+                                    of the persistent kernel looks at a flag that
+                                    nothing sets and gives up after 50 ms; the
+                                    kernel ends and fpm_get_stats / the getters
+                                    report FPM_ETIMEOUT.  The state is then
+                                    undefined (reload before further use).    */
 
 typedef struct fpm_plan fpm_plan;
 typedef struct fpm_server fpm_server;
@@ -190,8 +197,10 @@ FPM_API int fpm_load_tiles(fpm_plan *plan, const void *stack, int32_t dtype, int
  * was when the wave started; their pupil corrections are added in sequence
  * order when the wave ends.  `mode` is FPM_RUN_PLAIN, FPM_RUN_WAVES or
  * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH (and, with FPM_RUN_WAVES,
- * | FPM_RUN_TIMED); all modes give the same result.  FPM_ESTATE before fpm_load_tiles; FPM_ETIMEOUT if a bounded device
- * wait of the persistent kernel gave up (the state is then undefined).
+ * | FPM_RUN_TIMED); all modes give the same result.  FPM_ESTATE before
+ * fpm_load_tiles.  The call only enqueues work: a persistent run whose bounded
+ * device wait gave up is reported as FPM_ETIMEOUT by the next fpm_get_stats,
+ * fpm_get_spectrum or fpm_get_pupil (the state is then undefined).
  */
 FPM_API int fpm_reconstruct(fpm_plan *plan, int32_t iters, int32_t mode, void *stream);
 
@@ -220,10 +229,14 @@ typedef struct {
   int64_t update_launches;  /* fused-update launches of the last FPM_RUN_TIMED run     */
   int64_t updates;          /* LED updates those launches performed                    */
   double update_ms;         /* summed device time of those launches, milliseconds      */
+  int32_t device_error;     /* 0, or FPM_ETIMEOUT if a bounded device wait of the last
+                               persistent run gave up                                   */
+  int32_t persistent_clusters; /* clusters of the last persistent launch               */
 } fpm_stats;
 
-/* fpm_get_stats -- fill *out.  Waits for the events of the last FPM_RUN_TIMED
- * run (if any) to complete; update_ms is 0 when no timed run happened. */
+/* fpm_get_stats -- fill *out.  Synchronises the device; update_ms is 0 when no
+ * timed run happened.  Returns FPM_ETIMEOUT (with *out filled) when the last
+ * persistent run's device wait gave up. */
 FPM_API int fpm_get_stats(fpm_plan *plan, fpm_stats *out);
 
 /* fpm_initial_pupil -- the plan's initial pupil of `tile` (host memory,

@@ -24,6 +24,7 @@ U16, F32 = 0, 1
 RUN = {"plain": 0, "waves": 1, "persistent": 2}
 RUN_GRAPH = 0x100
 RUN_TIMED = 0x200
+RUN_FAULT_TEST = 0x400
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 
@@ -61,7 +62,8 @@ class PlanInfo(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
-                ("updates", C.c_int64), ("update_ms", C.c_double)]
+                ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
+                ("persistent_clusters", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -201,13 +203,16 @@ class Plan:
         self._stack_ref = stack if on_dev else None   # borrowed device memory stays alive
 
     def reconstruct(self, iters: int | None = None, mode: str = "waves", graph: bool = False, timed: bool = False,
-                    stream=None):
-        flag = RUN[mode] | (RUN_GRAPH if graph else 0) | (RUN_TIMED if timed else 0)
+                    stream=None, fault_test: bool = False):
+        flag = (RUN[mode] | (RUN_GRAPH if graph else 0) | (RUN_TIMED if timed else 0)
+                | (RUN_FAULT_TEST if fault_test else 0))
         _check(_lib.fpm_reconstruct(self._h, int(iters or self.iters), flag, _stream(stream)))
 
-    def stats(self) -> dict:
+    def stats(self, check: bool = True) -> dict:
         st = Stats()
-        _check(_lib.fpm_get_stats(self._h, C.byref(st)))
+        rc = _lib.fpm_get_stats(self._h, C.byref(st))
+        if check:
+            _check(rc)
         return st.as_dict()
 
     def spectrum(self, tile: int, out=None, stream=None):

@@ -88,7 +88,7 @@ __global__ void init_gather_kernel(float2 *out, const Img *stack, long long stri
 }
 
 // spec[t][N/2 + ky][N/2 + kx] = scale * X[t][ky mod m][kx mod m], ky, kx in [-m/2, m/2)
-__global__ void init_place_kernel(float2 *spec, const float2 *x, int m, int n, int n_tiles, float scale) {
+static __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, int n, int n_tiles, float scale) {
   const long long total = (long long)n_tiles * m * m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -101,18 +101,15 @@ __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, int n, i
 }
 
 // Add the wave's pupil corrections in slot (= sequence) order and compute
-// max |P|^2 over the support.  Grid: (merge entries, kNormParts); CTA (e, c)
-// handles row chunk c of entry e = (tile, slots) and writes the chunk's
-// maximum to pnorm_part[tile][c]; readers take the max of the kNormParts
-// values, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
-                                                    float *__restrict__ pnorm_part, const int2 *__restrict__ merges,
-                                                    const int2 *__restrict__ chords, int y_lo, int rows, int m,
-                                                    int slots) {
-  const int2 mg = merges[blockIdx.x];
-  const int t = mg.x, ns = mg.y;
+// max |P|^2 over the support.  The support rows are cut into kNormParts
+// chunks; chunk c of tile t writes its maximum to pnorm_part[t][c] and readers
+// take the max of the kNormParts values, so the result does not depend on
+// scheduling.  merge_chunk is one chunk done by one whole CTA.
+__device__ __forceinline__ void merge_chunk(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
+                                            float *__restrict__ pnorm_part, const int2 *__restrict__ chords, int t,
+                                            int ns, int chunk, int y_lo, int rows, int m, int slots) {
   const int rpp = (rows + kNormParts - 1) / kNormParts;
-  const int r0 = blockIdx.y * rpp, r1 = min(rows, r0 + rpp);
+  const int r0 = chunk * rpp, r1 = min(rows, r0 + rpp);
   const size_t mm = (size_t)m * m;
   float2 *p = pup + (size_t)t * mm;
   float mx = 0.f;
@@ -138,19 +135,30 @@ __global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, co
   __shared__ float red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();                       // red may still be read by a previous call
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
     float v = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) pnorm_part[(size_t)t * kNormParts + blockIdx.y] = v;
+    if (threadIdx.x == 0) pnorm_part[(size_t)t * kNormParts + chunk] = v;
   }
+}
+
+// Grid: (merge entries (tile, slots), kNormParts chunks).
+static __global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
+                                                           float *__restrict__ pnorm_part,
+                                                           const int2 *__restrict__ merges,
+                                                           const int2 *__restrict__ chords, int y_lo, int rows, int m,
+                                                           int slots) {
+  const int2 mg = merges[blockIdx.x];
+  merge_chunk(pup, dpup, pnorm_part, chords, mg.x, mg.y, blockIdx.y, y_lo, rows, m, slots);
 }
 
 // Simulator: box of the unshifted DFT spectrum times the pupil, placed in
 // IDFT input order (the box's centred index b - m/2 taken modulo m).
-__global__ void sim_crop_kernel(float2 *box, const float2 *spec_dft, const float2 *pup, const int2 *shifts,
+static __global__ void sim_crop_kernel(float2 *box, const float2 *spec_dft, const float2 *pup, const int2 *shifts,
                                 int led, int n_leds, int m, int n, int n_tiles) {
   const long long total = (long long)n_tiles * m * m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -165,7 +173,7 @@ __global__ void sim_crop_kernel(float2 *box, const float2 *spec_dft, const float
   }
 }
 
-__global__ void sim_abs_kernel(float *out, const float2 *box, int led, int n_leds, int m, int n_tiles, float inv_n2) {
+static __global__ void sim_abs_kernel(float *out, const float2 *box, int led, int n_leds, int m, int n_tiles, float inv_n2) {
   const long long total = (long long)n_tiles * m * m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -58,7 +59,7 @@ struct fpm_plan {
   int32_t busy = 0;                 // > 0 while a server job owns the plan
 
   // cached step lists keyed by iteration count
-  std::vector<fpm::StepLists> step_cache;
+  std::deque<fpm::StepLists> step_cache;   // deque: references stay valid as it grows
 };
 
 namespace fpm {

@@ -13,6 +13,7 @@
 
 #include "aux_kernels.cuh"
 #include "internal.h"
+#include "persistent.h"
 #include "runtime.h"
 #include "update.cuh"
 
@@ -182,6 +183,8 @@ struct DeviceState {
   std::vector<int64_t> timed_steps;           // steps whose update launch was timed
   int64_t timed_updates = 0;
   bool timed_valid = false;
+  std::map<int32_t, QueueDev *> queues;        // persistent queues by loop count
+  int persistent_clusters = 0;
 };
 
 static void dfree(void *p) {
@@ -197,6 +200,7 @@ void destroy_device_state(fpm_plan *p) {
   cudaDeviceSynchronize();
   for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t ev : d->events) cudaEventDestroy(ev);
+  for (auto &kv : d->queues) free_queue(kv.second);
   for (auto &s : d->steps) {
     dfree(s.items);
     dfree(s.merges);
@@ -253,8 +257,8 @@ static int ensure_device_state(fpm_plan *p) {
   if ((rc = upload(&d->tw_fwd, tf.data(), tf.size() * sizeof(float2)))) return rc;
   std::vector<float2> tl = twiddles_line(p->m, -1);
   if ((rc = upload(&d->twl_fwd_m, tl.data(), tl.size() * sizeof(float2)))) return rc;
-  FPM_CK(cudaMalloc((void **)&d->err, sizeof(unsigned)));
-  FPM_CK(cudaMemset(d->err, 0, sizeof(unsigned)));
+  FPM_CK(cudaMalloc((void **)&d->err, 4 * sizeof(unsigned)));
+  FPM_CK(cudaMemset(d->err, 0, 4 * sizeof(unsigned)));
   const size_t smem = d->var->smem(rows);
   FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -421,6 +425,12 @@ int launch_merge(float2 *pup, const float2 *dpup, float *pnorm_part, const int2 
   return FPM_OK;
 }
 
+UpdateArgs plan_update_args(fpm_plan *p) { return make_args(p, nullptr); }
+
+int plan_image_dtype(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->dtype : -1; }
+
+unsigned *plan_error_word(fpm_plan *p) { return p->dev ? p->dev->err : nullptr; }
+
 // Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
 // With `timed`, CUDA events bracket every update launch (waves mode only).
 static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st, bool timed, bool capturing,
@@ -505,12 +515,71 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
   return fail(FPM_EINVAL, "unknown mode %d", mode);
 }
 
+// FPM_ETIMEOUT if the last persistent run's bounded wait gave up (synchronises).
+static int device_error(fpm_plan *p) {
+  DeviceState *d = p->dev;
+  if (!d || !d->err) return FPM_OK;
+  unsigned e[2] = {0, 0};
+  FPM_CK(cudaDeviceSynchronize());
+  FPM_CK(cudaMemcpy(e, d->err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e[0]) return fail(FPM_ETIMEOUT, "a bounded device wait of the persistent kernel gave up (error bits 0x%x)", e[0]);
+  return FPM_OK;
+}
+
+int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool stall_test) {
+  DeviceState *d = p->dev;
+  auto it = d->queues.find(iters);
+  if (it == d->queues.end()) {
+    QueueDev *q = nullptr;
+    int rc = make_queue({QueueJob{p, iters}}, &q);
+    if (rc) return rc;
+    it = d->queues.emplace(iters, q).first;
+  }
+  QueueDev *q = it->second;
+  if (!graph || stall_test) {
+    int rc = launch_queue(q, d->err, stall_test ? 1 : 0, st, &d->persistent_clusters);
+    d->run_launches = 1;
+    return rc;
+  }
+  GraphKey key{iters, FPM_RUN_PERSISTENT | FPM_RUN_GRAPH, st};
+  auto g = d->graphs.find(key);
+  if (g == d->graphs.end()) {
+    cudaStream_t cap = st;
+    bool own = false;
+    if (cap == nullptr) {
+      FPM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+    }
+    FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_queue(q, d->err, 0, cap, &d->persistent_clusters);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &gr);
+    if (own) cudaStreamDestroy(cap);
+    if (rc) {
+      if (gr) cudaGraphDestroy(gr);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    g = d->graphs.emplace(key, ex).first;
+  }
+  FPM_CK(cudaGraphLaunch(g->second, st));
+  d->run_launches = 1;
+  return FPM_OK;
+}
+
 int get_stats(fpm_plan *p, fpm_stats *out) {
   std::memset(out, 0, sizeof(*out));
   DeviceState *d = p->dev;
   if (!d) return FPM_OK;
   out->load_launches = d->load_launches;
   out->run_launches = d->run_launches;
+  out->persistent_clusters = d->persistent_clusters;
+  const int derr = device_error(p);
+  out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
   if (d->timed_valid && !d->timed_steps.empty()) {
     FPM_CK(cudaEventSynchronize(d->events[2 * d->timed_steps.back() + 1]));
     double ms = 0;
@@ -523,7 +592,7 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
     out->update_launches = (int64_t)d->timed_steps.size();
     out->updates = d->timed_updates;
   }
-  return FPM_OK;
+  return derr;
 }
 
 }  // namespace fpm
@@ -537,6 +606,15 @@ int fpm_load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_dev
   fpm::clear_error();
   if (!p || !stack) return fail(FPM_EINVAL, "fpm_load_tiles: null argument");
   if (p->busy) return fail(FPM_EBUSY, "plan is owned by a server job");
+  return fpm::load_tiles(p, stack, dtype, on_device, stride_led, stride_row, counts_per_unit, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace fpm {
+
+int validate_stack(fpm_plan *p, const void *stack, int32_t dtype, int64_t stride_led, int64_t stride_row,
+                   float counts_per_unit, size_t *bytes) {
   if (dtype != FPM_U16 && dtype != FPM_F32) return fail(FPM_EINVAL, "unknown image dtype %d", dtype);
   if (!(counts_per_unit > 0) || !std::isfinite(counts_per_unit))
     return fail(FPM_EINVAL, "counts_per_unit must be positive and finite");
@@ -545,14 +623,23 @@ int fpm_load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_dev
     return fail(FPM_EINVAL, "strides (%lld, %lld) smaller than the image", (long long)stride_led, (long long)stride_row);
   if ((stride_row * es) % 16 || (stride_led * es) % 16 || ((uintptr_t)stack % 16))
     return fail(FPM_EINVAL, "stack base, rows and LED planes must be 16-byte aligned");
-  int rc;
-  if ((rc = fpm::ensure_device_state(p))) return rc;
-  fpm::DeviceState *d = p->dev;
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t bytes = (size_t)((p->n_leds - 1) * stride_led + (int64_t)(p->sensor_h - 1) * stride_row + p->sensor_w) * es;
+  if (bytes)
+    *bytes = (size_t)((p->n_leds - 1) * stride_led + (int64_t)(p->sensor_h - 1) * stride_row + p->sensor_w) * es;
+  return FPM_OK;
+}
+
+int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
+               int64_t stride_row, float counts_per_unit, cudaStream_t st) {
+  if (!stack) return fail(FPM_EINVAL, "fpm_load_tiles: null stack");
+  size_t bytes = 0;
+  int rc = validate_stack(p, stack, dtype, stride_led, stride_row, counts_per_unit, &bytes);
+  if (rc) return rc;
+  if ((rc = ensure_device_state(p))) return rc;
+  DeviceState *d = p->dev;
   if (on_device) {
     cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, stack) != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+    if (cudaPointerGetAttributes(&at, stack) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
       cudaGetLastError();
       return fail(FPM_EINVAL, "on_device stack is not device memory");
     }
@@ -573,10 +660,20 @@ int fpm_load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_dev
   d->stride_led = stride_led;
   d->stride_row = stride_row;
   d->inv_counts = 1.0f / counts_per_unit;
-  if ((rc = fpm::run_init(p, st))) return rc;
+  FPM_CK(cudaMemsetAsync(d->err, 0, 4 * sizeof(unsigned), st));   // a reload clears a previous failure
+  if ((rc = run_init(p, st))) return rc;
   d->loaded = true;
   return FPM_OK;
 }
+
+size_t plan_device_bytes(const fpm_plan *p) {
+  const size_t T = p->n_tiles, n = p->n, m = p->m;
+  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1) + T * kNormParts * 4;
+}
+
+}  // namespace fpm
+
+extern "C" {
 
 int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   fpm::clear_error();
@@ -587,13 +684,15 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   const int base = mode & 0xff;
   const bool graph = (mode & FPM_RUN_GRAPH) != 0;
   const bool timed = (mode & FPM_RUN_TIMED) != 0;
-  if ((mode & ~(0xff | FPM_RUN_GRAPH | FPM_RUN_TIMED)) ||
+  const bool stall = (mode & FPM_RUN_FAULT_TEST) != 0;
+  if ((mode & ~(0xff | FPM_RUN_GRAPH | FPM_RUN_TIMED | FPM_RUN_FAULT_TEST)) ||
       (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT))
     return fail(FPM_EINVAL, "unknown mode 0x%x", mode);
   if (timed && base != FPM_RUN_WAVES) return fail(FPM_EINVAL, "FPM_RUN_TIMED needs FPM_RUN_WAVES");
+  if (stall && base != FPM_RUN_PERSISTENT) return fail(FPM_EINVAL, "FPM_RUN_FAULT_TEST needs FPM_RUN_PERSISTENT");
   cudaStream_t st = (cudaStream_t)stream;
   fpm::DeviceState *d = p->dev;
-  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph);
+  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph, stall);
   if (!graph) {
     int64_t nl = 0;
     int rc = fpm::enqueue_reconstruct(p, iters, base, st, timed, false, &nl);
@@ -653,9 +752,14 @@ int fpm_get_stats(fpm_plan *p, fpm_stats *out) {
   return fpm::get_stats(p, out);
 }
 
-static int copy_out(const void *src, void *dst, size_t bytes, int32_t on_device, cudaStream_t st) {
+static int copy_out(fpm_plan *p, const void *src, void *dst, size_t bytes, int32_t on_device, cudaStream_t st) {
   FPM_CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  if (!on_device) FPM_CK(cudaStreamSynchronize(st));
+  if (!on_device) {
+    FPM_CK(cudaStreamSynchronize(st));
+    unsigned e = 0;
+    FPM_CK(cudaMemcpy(&e, p->dev->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) return fail(FPM_ETIMEOUT, "a bounded device wait of the last persistent run gave up");
+  }
   return FPM_OK;
 }
 
@@ -665,7 +769,7 @@ int fpm_get_spectrum(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, vo
   if (tile < 0 || tile >= p->n_tiles) return fail(FPM_EINVAL, "tile %d out of range", tile);
   if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
   const size_t nn = (size_t)p->n * p->n;
-  return copy_out(p->dev->spec + (size_t)tile * nn, dst, nn * sizeof(float2), on_device, (cudaStream_t)stream);
+  return copy_out(p, p->dev->spec + (size_t)tile * nn, dst, nn * sizeof(float2), on_device, (cudaStream_t)stream);
 }
 
 int fpm_get_pupil(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void *stream) {
@@ -674,7 +778,7 @@ int fpm_get_pupil(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void 
   if (tile < 0 || tile >= p->n_tiles) return fail(FPM_EINVAL, "tile %d out of range", tile);
   if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
   const size_t mm = (size_t)p->m * p->m;
-  return copy_out(p->dev->pup + (size_t)tile * mm, dst, mm * sizeof(float2), on_device, (cudaStream_t)stream);
+  return copy_out(p, p->dev->pup + (size_t)tile * mm, dst, mm * sizeof(float2), on_device, (cudaStream_t)stream);
 }
 
 int fpm_set_state(fpm_plan *p, int32_t tile, const void *spectrum, const void *pupil, void *stream) {

@@ -10,8 +10,8 @@
 namespace fpm {
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
                      long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st);
-// Persistent batched execution of `iters` loops of one plan (persistent.cu).
-int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph);
+// Persistent batched execution of `iters` loops of one plan.
+int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool stall_test);
 
 // The update-kernel variant for tile side m with `rows` support rows: its
 // factorisation m = a * b, cluster size and threads; false if none fits.
@@ -21,6 +21,20 @@ void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd);
 // Launch the update kernel over items [item0, item0 + count) (image dtype FPM_U16 or FPM_F32).
 int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
                         cudaStream_t st);
+// Validate an image stack description; *bytes (if set) = its extent in bytes.
+int validate_stack(fpm_plan *p, const void *stack, int32_t dtype, int64_t stride_led, int64_t stride_row,
+                   float counts_per_unit, size_t *bytes);
+// fpm_load_tiles without the ownership check (the server loads the plans it owns).
+int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
+               int64_t stride_row, float counts_per_unit, cudaStream_t st);
+// Device bytes a plan's state takes once loaded (spectra, pupils, corrections).
+size_t plan_device_bytes(const fpm_plan *p);
+// Device-side description of a loaded plan for the update kernel (items unset).
+UpdateArgs plan_update_args(fpm_plan *p);
+// Image element type of a loaded plan (FPM_U16 / FPM_F32); -1 if not loaded.
+int plan_image_dtype(const fpm_plan *p);
+// The plan's device error word ([0] code, [1] abort flag), or null.
+unsigned *plan_error_word(fpm_plan *p);
 // Launch the pupil merge / normaliser over `count` (tile, slots) entries.
 int launch_merge(float2 *pup, const float2 *dpup, float *pnorm_part, const int2 *merges, int count,
                  const int2 *chords, int y_lo, int rows, int m, int slots, cudaStream_t st);

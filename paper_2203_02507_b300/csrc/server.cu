@@ -2,11 +2,6 @@
 #include "internal.h"
 #include "runtime.h"
 
-namespace fpm {
-int run_persistent(fpm_plan *, int32_t, cudaStream_t, bool) {
-  return fail(FPM_ESTATE, "persistent mode is not available in this build");
-}
-}  // namespace fpm
 
 extern "C" {
 int fpm_server_create(size_t, fpm_server **out) {

@@ -136,11 +136,12 @@ def test_one_iteration_matches_oracle(name):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("name", ["m64_epry", "m256_epry"])
+@pytest.mark.parametrize("name", ["m64_epry", "m128_epry", "m192_epry", "m256_epry", "tile64_plain"])
 def test_execution_modes_are_bit_identical(name):
     j = job(name)
     res = []
-    for mode, graph in [("waves", False), ("plain", False), ("waves", True)]:
+    for mode, graph in [("waves", False), ("plain", False), ("waves", True), ("persistent", False),
+                        ("persistent", True)]:
         p = j.plan(iters=2)
         p.load_tiles(j.stack, j.counts_per_unit)
         p.reconstruct(2, mode=mode, graph=graph)
@@ -210,4 +211,28 @@ def test_largest_hr_grid_upsample8():
                                      n, 1, True)
     assert rel_l2(p.spectrum(0), spec) < SPEC_TOL
     assert rel_l2(p.pupil(0), pup) < PUPIL_TOL
+    p.close()
+
+
+def test_persistent_wait_timeout_is_reported_and_recoverable():
+    """The bounded dependency wait of the persistent kernel gives up (test hook:
+    every wait looks at a flag nothing sets, 50 ms limit); the kernel ends, the
+    host reads FPM_ETIMEOUT, and the plan works again after a reload."""
+    from paper_2203_02507_b300 import FpmError
+    from paper_2203_02507_b300._fpm import ETIMEOUT
+    j = job("m64_epry9")
+    p = j.plan(iters=1)
+    p.load_tiles(j.stack, j.counts_per_unit)
+    p.reconstruct(1, mode="persistent", fault_test=True)
+    st = p.stats(check=False)
+    assert st["device_error"] == ETIMEOUT
+    with pytest.raises(FpmError) as e:
+        p.stats()
+    assert e.value.code == ETIMEOUT
+    # a normal run after reloading gives the oracle's answer again
+    p.load_tiles(j.stack, j.counts_per_unit)
+    p.reconstruct(1, mode="persistent")
+    assert p.stats()["device_error"] == 0
+    spec, _ = j.oracle_tile(0, 1)
+    assert rel_l2(p.spectrum(0), spec) < SPEC_TOL
     p.close()
