@@ -255,17 +255,30 @@ FPM_API int fpm_simulate(fpm_plan *plan, const void *objects, float *out, void *
 
 /* ---- serving: continuous batching of many jobs ---------------------------- */
 
-/* fpm_server_create -- start a server that runs the jobs given to it on the
- * current device, admitting them while their device memory fits
- * `hbm_budget_bytes`.  */
+/* fpm_server_create -- start a server (one worker thread) that runs the jobs
+ * given to it on the current device, admitting them while their device memory
+ * fits `hbm_budget_bytes`.  */
 FPM_API int fpm_server_create(size_t hbm_budget_bytes, fpm_server **out);
 
 /*
- * fpm_submit -- queue `iters` iteration loops of a loaded plan as a job
- * (non-blocking).  The plan belongs to the server until the job is DONE or
- * FAILED.  FPM_EBUDGET if the plan alone exceeds the budget.
+ * fpm_submit -- queue `iters` (1..plan iters) loops of a plan as a job
+ * (non-blocking).  Either `stack` is NULL and the plan is already loaded
+ * (fpm_load_tiles), or `stack` and the following arguments describe its images
+ * exactly as fpm_load_tiles takes them and the server loads them when it admits
+ * the job; host memory given this way must stay valid and unchanged until the
+ * job is DONE or FAILED.  The job is charged the plan's device state plus the
+ * copied stack; FPM_EBUDGET if that alone exceeds the budget.  Jobs are
+ * admitted first come first served while the admitted jobs fit the budget; a
+ * job gives its charge back when it finishes (its spectra and pupils stay on
+ * the device until the caller destroys the plan).  The plan belongs to the
+ * server (FPM_EBUSY for other calls on it) until the job is DONE or FAILED.
+ * The server runs the admitted jobs' wave steps together in rounds of one
+ * persistent launch each, so jobs that arrive while others run join at the
+ * next round; each job computes what fpm_reconstruct(plan, iters) computes.
  */
-FPM_API int fpm_submit(fpm_server *server, fpm_plan *plan, int32_t iters, fpm_job *out);
+FPM_API int fpm_submit(fpm_server *server, fpm_plan *plan, int32_t iters, const void *stack, int32_t dtype,
+                       int32_t on_device, int64_t stride_led, int64_t stride_row, float counts_per_unit,
+                       fpm_job *out);
 
 #define FPM_JOB_QUEUED  0
 #define FPM_JOB_RUNNING 1
@@ -276,7 +289,8 @@ FPM_API int fpm_submit(fpm_server *server, fpm_plan *plan, int32_t iters, fpm_jo
  * admit and submit -> done times in seconds (0 while unknown).  */
 FPM_API int fpm_poll(fpm_server *server, fpm_job job, int32_t *state, double *wait_s, double *latency_s);
 
-/* fpm_server_destroy -- finish or cancel queued jobs, stop the server, free it. */
+/* fpm_server_destroy -- let admitted jobs finish, cancel (FAILED) jobs not yet
+ * admitted, stop the worker and free the server.  Plans are given back. */
 FPM_API int fpm_server_destroy(fpm_server *server);
 
 /*

@@ -84,7 +84,7 @@ _SIGS = {
     "fpm_get_stats": [_vp, C.POINTER(Stats)],
     "fpm_simulate": [_vp, _vp, _vp, _vp],
     "fpm_server_create": [C.c_size_t, C.POINTER(_vp)],
-    "fpm_submit": [_vp, _vp, _i32, C.POINTER(_i64)],
+    "fpm_submit": [_vp, _vp, _i32, _vp, _i32, _i32, _i64, _i64, _f32, C.POINTER(_i64)],
     "fpm_poll": [_vp, _i64, C.POINTER(_i32), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "fpm_server_destroy": [_vp],
     "fpm_update_tile_static": [_vp, _i32, _vp, _i32, _vp, _i32, _i32, C.c_double, C.c_double, C.c_double, _i32, _vp],
@@ -257,9 +257,18 @@ class Server:
         _check(_lib.fpm_server_create(int(hbm_budget_bytes), C.byref(h)))
         self._h = h
 
-    def submit(self, plan: Plan, iters: int | None = None) -> int:
+    def submit(self, plan: Plan, iters: int | None = None, stack=None, counts_per_unit: float = 1.0) -> int:
+        """Queue a job.  With `stack` ([L, H, W] uint16/float32, host or device) the
+        server loads the images at admission; keep `stack` alive until the job ends."""
         job = _i64()
-        _check(_lib.fpm_submit(self._h, plan._h, int(iters or plan.iters), C.byref(job)))
+        if stack is None:
+            args = (None, 0, 0, 0, 0, 1.0)
+        else:
+            code = F32 if str(stack.dtype).endswith("float32") else U16
+            l_n, h, w = stack.shape
+            args = (_ptr(stack), code, 1 if _is_device(stack) else 0, int(h * w), int(w), float(counts_per_unit))
+            plan._stack_ref = stack
+        _check(_lib.fpm_submit(self._h, plan._h, int(iters or plan.iters), *args, C.byref(job)))
         return job.value
 
     def poll(self, job: int):

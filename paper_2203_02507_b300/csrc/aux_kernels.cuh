@@ -83,7 +83,7 @@ __global__ void init_gather_kernel(float2 *out, const Img *stack, long long stri
     float v;
     if constexpr (sizeof(Img) == 2) v = (float)reinterpret_cast<const unsigned short *>(stack)[off];
     else v = reinterpret_cast<const float *>(stack)[off];
-    out[i] = make_float2(sqrtf(fmaxf(v * inv_counts, 0.f)), 0.f);
+    out[i] = make_float2(sqrtf(fmaxf(__fmul_rn(v, inv_counts), 0.f)), 0.f);
   }
 }
 
@@ -130,7 +130,7 @@ __device__ __forceinline__ void merge_chunk(float2 *__restrict__ pup, const floa
       for (; s < ns; ++s) v = cadd(v, d[(size_t)s * mm]);
       p[off] = v;
     }
-    mx = fmaxf(mx, v.x * v.x + v.y * v.y);
+    mx = fmaxf(mx, cabs2(v));
   }
   __shared__ float red[32];
 #pragma unroll
@@ -180,7 +180,7 @@ static __global__ void sim_abs_kernel(float *out, const float2 *box, int led, in
     const int t = (int)(i / ((long long)m * m));
     const long long px = i % ((long long)m * m);
     const float2 v = cscale(box[i], inv_n2);
-    out[((size_t)t * n_leds + led) * m * m + px] = v.x * v.x + v.y * v.y;
+    out[((size_t)t * n_leds + led) * m * m + px] = cabs2(v);
   }
 }
 

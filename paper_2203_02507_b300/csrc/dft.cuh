@@ -1,5 +1,10 @@
 // Small DFTs held entirely in registers: the butterflies of the tile FFTs.
 //
+// Products are written with explicit round-to-nearest intrinsics (__fmul_rn,
+// __fmaf_rn) so that the compiler cannot contract or reassociate them
+// differently in different kernels: every kernel that inlines these helpers
+// computes bit-identical results.
+//
 // dft<R, S>(v) replaces v[0..R) by X[k] = sum_n v[n] exp(S * 2 pi i n k / R),
 // natural order in and out.  S = +1 is the inverse direction (no 1/R factor),
 // S = -1 the forward one.  Twiddles inside a DFT are exact constants of the
@@ -12,13 +17,15 @@ namespace fpm {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 // a * conj(b)
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
-  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+  return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)));
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
+// |a|^2
+__device__ __forceinline__ float cabs2(float2 a) { return __fmaf_rn(a.x, a.x, __fmul_rn(a.y, a.y)); }
 // multiply by S*i
 template <int S>
 __device__ __forceinline__ float2 mul_si(float2 a) {
@@ -28,7 +35,7 @@ __device__ __forceinline__ float2 mul_si(float2 a) {
 template <int S>
 __device__ __forceinline__ float2 mul_cs(float2 a, float c, float s) {
   const float ss = S > 0 ? s : -s;
-  return make_float2(a.x * c - a.y * ss, a.x * ss + a.y * c);
+  return make_float2(__fmaf_rn(a.x, c, -__fmul_rn(a.y, ss)), __fmaf_rn(a.x, ss, __fmul_rn(a.y, c)));
 }
 
 // cos(pi/8), sin(pi/8), sqrt(1/2), sqrt(3)/2
@@ -59,10 +66,10 @@ template <int S>
 __device__ __forceinline__ void dft3(float2 &a0, float2 &a1, float2 &a2) {
   const float2 s = cadd(a1, a2);
   const float2 d = mul_si<S>(csub(a1, a2));     // S i (a1 - a2)
-  const float2 m = make_float2(a0.x - 0.5f * s.x, a0.y - 0.5f * s.y);
+  const float2 m = make_float2(__fmaf_rn(-0.5f, s.x, a0.x), __fmaf_rn(-0.5f, s.y, a0.y));
   a0 = cadd(a0, s);
-  a1 = make_float2(m.x + FPM_R3 * d.x, m.y + FPM_R3 * d.y);
-  a2 = make_float2(m.x - FPM_R3 * d.x, m.y - FPM_R3 * d.y);
+  a1 = make_float2(__fmaf_rn(FPM_R3, d.x, m.x), __fmaf_rn(FPM_R3, d.y, m.y));
+  a2 = make_float2(__fmaf_rn(-FPM_R3, d.x, m.x), __fmaf_rn(-FPM_R3, d.y, m.y));
 }
 
 template <int R, int S>

@@ -276,6 +276,8 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
   return FPM_OK;
 }
 
+QueueDev *new_queue() { return new QueueDev(); }
+
 int make_queue(const std::vector<QueueJob> &jobs, QueueDev **out) {
   *out = nullptr;
   QueueDev *q = new QueueDev();

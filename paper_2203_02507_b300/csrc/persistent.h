@@ -24,6 +24,8 @@ struct QueueDev;   // device work queue, job table and counters
 // Flatten the jobs' wave steps into one queue (step-major, so that every
 // entry depends only on earlier ones): 8 ints per entry.
 int build_queue(const std::vector<QueueJob> &jobs, std::vector<int32_t> &items_out, int32_t *n_tiles_out);
+// An empty queue whose buffers grow on the first refill.
+QueueDev *new_queue();
 // Build and upload the queue of `jobs` (all loaded, same image type).
 int make_queue(const std::vector<QueueJob> &jobs, QueueDev **out);
 // Rebuild an existing queue for new jobs, reusing its device buffers when they

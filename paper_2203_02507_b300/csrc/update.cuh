@@ -139,7 +139,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         }
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) {
-          omax = fmaxf(omax, v[aa].x * v[aa].x + v[aa].y * v[aa].y);
+          omax = fmaxf(omax, cabs2(v[aa]));
           v[aa] = cmul(v[aa], pv[aa]);
         }
         Dft<A, 1>::run(v);
@@ -221,12 +221,12 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         // amplitude step at y = k1 + A k2
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const float in = fmaxf(meas[u][k2] * a.inv_counts, 0.f);
+          const float in = fmaxf(__fmul_rn(meas[u][k2], a.inv_counts), 0.f);
           const float2 f = v[k2];
-          const float m2 = f.x * f.x + f.y * f.y;
+          const float m2 = cabs2(f);
           if (m2 > 0.f) {
-            const float s = (in > 0.f) ? in * rsqrtf(in * m2) : 0.f;
-            v[k2] = make_float2(f.x * s, f.y * s);
+            const float s = (in > 0.f) ? __fmul_rn(in, rsqrtf(__fmul_rn(in, m2))) : 0.f;
+            v[k2] = cscale(f, s);
           } else {
             v[k2] = make_float2(sqrtf(in), 0.f);
           }
@@ -345,7 +345,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
             const float2 phi = cmul(o, p);
             const float2 d = csub(cscale(v[k2], a.scale), phi);
             const float2 pc = cmulc(d, p);        // D * conj(P)
-            srow[x] = make_float2(o.x + pc.x * inv_pn, o.y + pc.y * inv_pn);
+            srow[x] = make_float2(__fmaf_rn(pc.x, inv_pn, o.x), __fmaf_rn(pc.y, inv_pn, o.y));
             if (dp) {
               const float2 oc = cmulc(d, o);      // D * conj(O_old)
               dp[(size_t)by * M + x] = cscale(oc, inv_on);
