@@ -136,12 +136,33 @@ class ClockSampler:
 # synthetic data on the device
 # ---------------------------------------------------------------------------
 
-def device_stack(plan, w, torch, dev):
+def gpu_objects(torch, dev, n, tiles, seed, sigma=2.0):
+    """HR objects made on the GPU with the recipe's statistics: seeded N(0,1) fields,
+    periodic Gaussian smoothing (sigma = 2 HR px, applied in the Fourier domain),
+    min-max mapped to amplitude [0.5, 1] and phase [-pi/2, pi/2].  Used for the
+    large auxiliary workloads, where drawing every tile on the host would dominate."""
+    g = torch.Generator(device=dev).manual_seed(seed)
+    f = torch.fft.fftfreq(n, device=dev)
+    gauss = torch.exp(-2.0 * (math.pi * sigma) ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
+    out = torch.empty((tiles, n, n), dtype=torch.complex64, device=dev)
+    for t in range(tiles):
+        a, p = (torch.fft.ifft2(torch.fft.fft2(torch.randn((n, n), generator=g, device=dev)) * gauss).real
+                for _ in range(2))
+        a = 0.5 + 0.5 * (a - a.min()) / (a.max() - a.min())
+        p = ((p - p.min()) / (p.max() - p.min()) - 0.5) * math.pi
+        out[t] = torch.polar(a, p)
+    return out
+
+
+def device_stack(plan, w, torch, dev, fast=False):
     """Sensor stack [L, S, S] of 12-bit counts (int16 bits) simulated on the GPU."""
     t_n, n, m, l_n = w.n_tiles, w.hr, w.tile, w.n_leds
-    objs = torch.empty((t_n, n, n), dtype=torch.complex64, device=dev)
-    for t in range(t_n):
-        objs[t].copy_(torch.from_numpy(synth.hr_object(n, t, w.seed_offset).astype(np.complex64)))
+    if fast:
+        objs = gpu_objects(torch, dev, n, t_n, 1 + w.seed_offset)
+    else:
+        objs = torch.empty((t_n, n, n), dtype=torch.complex64, device=dev)
+        for t in range(t_n):
+            objs[t].copy_(torch.from_numpy(synth.hr_object(n, t, w.seed_offset).astype(np.complex64)))
     imgs = torch.empty((t_n, l_n, m, m), dtype=torch.float32, device=dev)
     plan.simulate(objs, imgs)
     del objs
@@ -235,6 +256,126 @@ def run_reference(args):
     return 0
 
 
+def aggregate(ms_local, updates_local, dist=None, device=None):
+    """Whole-job result of N independent replicas: the slowest rank's time and the
+    units all ranks processed.  Returns (ms, total_updates, updates_per_s)."""
+    import torch
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        u = torch.tensor([updates_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms_local, updates_local = float(t.item()), float(u.item())
+    return ms_local, updates_local, updates_local / (ms_local / 1e3)
+
+
+# ---------------------------------------------------------------------------
+# batched and served forms
+# ---------------------------------------------------------------------------
+
+def uneven_batch(torch, dev, steps=3):
+    """Three jobs (128/192/256 tiles, 9x9/13x13/15x15 LEDs, 15 loops, EPRY) in one
+    persistent launch per step; returns updates/s and ms per step."""
+    from paper_2203_02507_b300 import plan_for, reconstruct_batch
+    ws = [synth.WORKLOADS[k] for k in ("batch_m128", "batch_m192", "batch_m256")]
+    plans, stacks = [], []
+    for w in ws:
+        p = plan_for(w)
+        st, k = device_stack(p, w, torch, dev, fast=True)
+        p.load_tiles(st, k)
+        plans.append(p)
+        stacks.append((st, k))
+    upd = sum(w.updates for w in ws)
+
+    def step():
+        for p, (st, k) in zip(plans, stacks):
+            p.load_tiles(st, k)
+        reconstruct_batch(plans, [w.iters for w in ws], graph=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    for p in plans:
+        assert p.stats()["device_error"] == 0
+        p.close()
+    return {"value": upd / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "updates_per_step": upd, "steps": steps,
+            "jobs": [w.name for w in ws], "mode": "one persistent launch per step (graph)"}
+
+
+def plain_rate(torch, dev, w):
+    """Updates/s of the plain path (one tile at a time, one LED per launch) on one loop of `w`."""
+    from paper_2203_02507_b300 import plan_for
+    p = plan_for(w, iters=1)
+    st, k = device_stack(p, w, torch, dev, fast=True)
+    p.load_tiles(st, k)
+    p.reconstruct(1, mode="waves")
+    p.load_tiles(st, k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p.reconstruct(1, mode="plain")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    p.close()
+    return w.n_tiles * w.n_leds / dt
+
+
+def serving(torch, dev, n_jobs, budget=120 << 30):
+    """The first n_jobs of the serving stream (Poisson arrivals at 2 jobs/s) through
+    the server in real time; latency = submit -> done."""
+    from paper_2203_02507_b300 import Server, plan_for
+    stream = synth.serving_jobs(500)[:n_jobs]
+    prepared = []
+    for arrival, w in stream:
+        p = plan_for(w)
+        st, k = device_stack(p, w, torch, dev, fast=True)
+        prepared.append((arrival, w, p, st, k))
+    torch.cuda.synchronize()
+    srv = Server(budget)
+    ids = []
+    t0 = time.perf_counter()
+    for arrival, w, p, st, k in prepared:
+        while time.perf_counter() - t0 < arrival:
+            time.sleep(0.0005)
+        ids.append(srv.submit(p, w.iters, stack=st, counts_per_unit=k))
+    while True:
+        states = [srv.poll(i) for i in ids]
+        if all(s[0] in ("done", "failed") for s in states):
+            break
+        time.sleep(0.002)
+    t_end = time.perf_counter() - t0
+    srv.close()
+    assert all(s[0] == "done" for s in states), states
+    lat = np.array([s[2] for s in states])
+    upd = sum(w.updates for _, w, _, _, _ in prepared)
+    # plain path, same arrivals: one job at a time (FIFO), each at the plain rate measured for its tile size
+    rates = {}
+    for m in sorted({w.tile for _, w, _, _, _ in prepared}):
+        rates[m] = plain_rate(torch, dev, synth.Workload(f"plain{m}", sensor=4 * m, tile=m, tiles=4, overlap=0,
+                                                         iters=1, epry=True, optics=synth.Optics(led_side=15)))
+    free_at, plain_lat = 0.0, []
+    for arrival, w, _, _, _ in prepared:
+        start = max(arrival, free_at)
+        free_at = start + w.updates / rates[w.tile]
+        plain_lat.append(free_at - arrival)
+    for _, _, p, _, _ in prepared:
+        p.close()
+    plain_lat = np.array(plain_lat)
+    return {"jobs": n_jobs, "arrivals": "Poisson 2 jobs/s (first jobs of the 500-job stream)",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "updates_per_s": upd / t_end, "updates": upd, "wall_s": t_end,
+            "plain_path_model": {"p50_s": float(np.percentile(plain_lat, 50)),
+                                 "p99_s": float(np.percentile(plain_lat, 99)),
+                                 "plain_updates_per_s_by_tile": {str(k): v for k, v in rates.items()},
+                                 "how": "FIFO, one job at a time at the plain path's measured per-tile-size rate"},
+            "budget_gb": budget / (1 << 30)}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -248,6 +389,7 @@ def main():
     ap.add_argument("--workload", default="fov2048_m256")
     ap.add_argument("--mode", default="waves", choices=["waves", "persistent"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
+    ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,12 +436,8 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     st = plan.stats()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, _, value = aggregate(ms, w.updates * args.steps, dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
-    value = world * w.updates / (ms_per_step / 1e3)
     launches = (st["load_launches"] + st["run_launches"]) * args.steps
 
     # roofline of the fused update kernel from the event-timed launches of the last step
@@ -365,6 +503,23 @@ def main():
         line["plain_path"] = {"value": plain_upd / plain_s, "unit": UNIT,
                               "sample": f"one loop of all {w.n_tiles} tiles ({plain_upd} updates), no graph",
                               "speedup_of_batched": value / (plain_upd / plain_s)}
+        # the same FOV step in persistent mode (one launch per step, graph)
+        plan.load_tiles(stack, k)
+        plan.reconstruct(w.iters, mode="persistent", graph=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.load_tiles(stack, k)
+            plan.reconstruct(w.iters, mode="persistent", graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / args.steps
+        line["persistent_path"] = {"value": w.updates / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                                   "clusters": plan.stats()["persistent_clusters"]}
+        del host_stack, host_out
+        line["uneven_batch"] = uneven_batch(torch, dev)
+        if args.serving_jobs > 0:
+            line["serving"] = serving(torch, dev, args.serving_jobs)
         if world == 1:
             v, upd, wall = cpu_baseline(w.name, tiles=1, iters=4, procs=1)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -205,6 +205,18 @@ FPM_API int fpm_load_tiles(fpm_plan *plan, const void *stack, int32_t dtype, int
 FPM_API int fpm_reconstruct(fpm_plan *plan, int32_t iters, int32_t mode, void *stream);
 
 /*
+ * fpm_reconstruct_batch -- run `iters[i]` loops of each of `n` loaded plans
+ * together in one persistent launch (tiles of different sizes from different
+ * jobs share the device work queue; Sec. 3.1's independent sub-regions).
+ * Every plan must be loaded with the same image type.  `mode` is
+ * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH.  Each plan ends exactly as
+ * fpm_reconstruct(plan, iters[i]) leaves it.  Errors as fpm_reconstruct;
+ * a device-wait timeout is reported by each plan's fpm_get_stats.
+ */
+FPM_API int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t n, int32_t mode,
+                                  void *stream);
+
+/*
  * fpm_get_spectrum / fpm_get_pupil -- copy tile `tile`'s current N x N spectrum
  * (m x m pupil), centred complex64, to `dst` (host memory if on_device == 0,
  * device memory otherwise).  Stream-ordered; for host `dst` the call returns

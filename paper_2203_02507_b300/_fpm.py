@@ -87,6 +87,7 @@ _SIGS = {
     "fpm_submit": [_vp, _vp, _i32, _vp, _i32, _i32, _i64, _i64, _f32, C.POINTER(_i64)],
     "fpm_poll": [_vp, _i64, C.POINTER(_i32), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "fpm_server_destroy": [_vp],
+    "fpm_reconstruct_batch": [C.POINTER(_vp), C.POINTER(_i32), _i32, _i32, _vp],
     "fpm_update_tile_static": [_vp, _i32, _vp, _i32, _vp, _i32, _i32, C.c_double, C.c_double, C.c_double, _i32, _vp],
 }
 for _name, _args in _SIGS.items():
@@ -286,6 +287,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def reconstruct_batch(plans, iters=None, graph: bool = False, stream=None):
+    """Run several loaded plans together in one persistent launch (fpm_reconstruct_batch)."""
+    n = len(plans)
+    hs = (_vp * n)(*[p._h.value for p in plans])
+    its = (_i32 * n)(*[int(i) for i in (iters or [p.iters for p in plans])])
+    _check(_lib.fpm_reconstruct_batch(hs, its, n, RUN["persistent"] | (RUN_GRAPH if graph else 0), _stream(stream)))
 
 
 def update_tile_static(spectrum, pupil, image, shift, wavelength_um, na, pixel_um, epry, stream=None):

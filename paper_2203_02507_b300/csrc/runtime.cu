@@ -191,6 +191,8 @@ static void dfree(void *p) {
   if (p) cudaFree(p);
 }
 
+void forget_batches(fpm_plan *p);
+
 void destroy_device_state(fpm_plan *p) {
   DeviceState *d = p->dev;
   if (!d) return;
@@ -201,6 +203,7 @@ void destroy_device_state(fpm_plan *p) {
   for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t ev : d->events) cudaEventDestroy(ev);
   for (auto &kv : d->queues) free_queue(kv.second);
+  forget_batches(p);
   for (auto &s : d->steps) {
     dfree(s.items);
     dfree(s.merges);
@@ -571,6 +574,98 @@ int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool
   return FPM_OK;
 }
 
+// Batches of several plans: one queue per distinct batch (cached by its plans and
+// loop counts), the error words of every plan reset and pointed at the first's.
+struct BatchKey {
+  std::vector<fpm_plan *> plans;
+  std::vector<int32_t> iters;
+  cudaStream_t st;
+  bool graph;
+  bool operator<(const BatchKey &o) const {
+    if (plans != o.plans) return plans < o.plans;
+    if (iters != o.iters) return iters < o.iters;
+    if (st != o.st) return st < o.st;
+    return graph < o.graph;
+  }
+};
+struct BatchEntry {
+  QueueDev *q = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+static std::mutex g_batch_mu;
+static std::map<BatchKey, BatchEntry> g_batches;
+
+void forget_batches(fpm_plan *p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_batches.begin(); it != g_batches.end();) {
+    if (std::find(it->first.plans.begin(), it->first.plans.end(), p) != it->first.plans.end()) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      free_queue(it->second.q);
+      it = g_batches.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+int run_batch(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph) {
+  BatchKey key;
+  for (const QueueJob &j : jobs) {
+    key.plans.push_back(j.plan);
+    key.iters.push_back(j.iters);
+  }
+  key.st = st;
+  key.graph = graph;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  auto it = g_batches.find(key);
+  if (it == g_batches.end()) {
+    BatchEntry e;
+    int rc = make_queue(jobs, &e.q);
+    if (rc) return rc;
+    it = g_batches.emplace(key, e).first;
+  }
+  BatchEntry &e = it->second;
+  unsigned *err = jobs[0].plan->dev->err;
+  for (size_t k = 1; k < jobs.size(); ++k)
+    FPM_CK(cudaMemsetAsync(jobs[k].plan->dev->err, 0, 4 * sizeof(unsigned), st));
+  int clusters = 0;
+  if (!graph) {
+    int rc = launch_queue(e.q, err, 0, st, &clusters);
+    if (rc) return rc;
+  } else {
+    if (!e.exec) {
+      cudaStream_t cap = st;
+      bool own = false;
+      if (cap == nullptr) {
+        FPM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        own = true;
+      }
+      FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      int rc = launch_queue(e.q, err, 0, cap, &clusters);
+      cudaGraph_t gr = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(cap, &gr);
+      if (own) cudaStreamDestroy(cap);
+      if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (ce != cudaSuccess) return fail(FPM_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&e.exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ce != cudaSuccess) return fail(FPM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    FPM_CK(cudaGraphLaunch(e.exec, st));
+  }
+  // the batch reports its device errors through the first plan; copy the word to the others
+  for (size_t k = 1; k < jobs.size(); ++k)
+    FPM_CK(cudaMemcpyAsync(jobs[k].plan->dev->err, err, 2 * sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  for (const QueueJob &j : jobs) {
+    j.plan->dev->run_launches = 1;
+    if (clusters) j.plan->dev->persistent_clusters = clusters;
+  }
+  return FPM_OK;
+}
+
 int get_stats(fpm_plan *p, fpm_stats *out) {
   std::memset(out, 0, sizeof(*out));
   DeviceState *d = p->dev;
@@ -745,6 +840,25 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   FPM_CK(cudaGraphLaunch(it->second, st));
   d->run_launches = d->graph_launches[key];
   return FPM_OK;
+}
+
+int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t n, int32_t mode, void *stream) {
+  fpm::clear_error();
+  if (!plans || !iters || n < 1) return fail(FPM_EINVAL, "fpm_reconstruct_batch: empty batch");
+  if ((mode & ~FPM_RUN_GRAPH) != FPM_RUN_PERSISTENT)
+    return fail(FPM_EINVAL, "fpm_reconstruct_batch runs FPM_RUN_PERSISTENT (optionally | FPM_RUN_GRAPH)");
+  std::vector<fpm::QueueJob> jobs;
+  for (int i = 0; i < n; ++i) {
+    fpm_plan *p = plans[i];
+    if (!p) return fail(FPM_EINVAL, "plan %d is null", i);
+    if (p->busy) return fail(FPM_EBUSY, "plan %d is owned by a server job", i);
+    if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "plan %d is not loaded", i);
+    if (iters[i] < 1 || iters[i] > p->iters) return fail(FPM_EINVAL, "plan %d: iters %d outside 1..%d", i, iters[i], p->iters);
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == p) return fail(FPM_EINVAL, "plan %d appears twice", i);
+    jobs.push_back(fpm::QueueJob{p, iters[i]});
+  }
+  return fpm::run_batch(jobs, (cudaStream_t)stream, (mode & FPM_RUN_GRAPH) != 0);
 }
 
 int fpm_get_stats(fpm_plan *p, fpm_stats *out) {

@@ -10,6 +10,9 @@
 namespace fpm {
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
                      long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st);
+struct QueueJob;
+// One persistent launch over several loaded plans (cached per batch).
+int run_batch(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph);
 // Persistent batched execution of `iters` loops of one plan.
 int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool stall_test);
 

@@ -128,3 +128,28 @@ def test_admission_by_budget_and_overlap():
     srv.close()
     for p in (pb, pb2, p1, p2):
         p.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_uneven_batch_in_one_persistent_launch(graph):
+    """Four jobs with tiles of 64, 128, 192 and 256 in one launch end exactly as run one by one."""
+    from paper_2203_02507_b300 import reconstruct_batch
+    plans = []
+    for w in MIX:
+        j = job(w)
+        p = j.plan()
+        p.load_tiles(j.stack, j.counts_per_unit)
+        plans.append(p)
+    reconstruct_batch(plans, [w.iters for w in MIX], graph=graph)
+    for w, p in zip(MIX, plans):
+        assert p.stats()["device_error"] == 0
+        j = job(w)
+        q = j.plan()
+        q.load_tiles(j.stack, j.counts_per_unit)
+        q.reconstruct(w.iters, mode="waves")
+        for t in range(w.n_tiles):
+            assert np.array_equal(p.spectrum(t), q.spectrum(t))
+            assert np.array_equal(p.pupil(t), q.pupil(t))
+        q.close()
+    for p in plans:
+        p.close()
