@@ -37,11 +37,10 @@ UNIT = "updates/s"
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
 
-# DRAM bytes per update of the fused update kernel (m = 256, EPRY), from the ncu
-# capture summarised in profiles/update_kernel_m256_ncu_full.md: 4,285,696 B read
-# and 0 B written for a launch of 9 updates.  A full launch scales it by its
-# updates.  Set to None whenever the kernel changes until it is re-captured.
-TRAFFIC_PER_UPDATE = {256: 4285696 / 9}
+# DRAM bytes per update of the update kernel (m -> bytes), from the latest ncu
+# capture in profiles/ of the kernel as it stands; a launch scales it by the
+# updates it processes.  Emptied whenever the kernel changes until re-captured.
+TRAFFIC_PER_UPDATE = {}
 
 EXTRA = {
     # small case of the same kernel for ncu captures: 3 x 3 tiles of 256, inputs > L2
@@ -387,7 +386,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fov2048_m256")
-    ap.add_argument("--mode", default="waves", choices=["waves", "persistent"])
+    ap.add_argument("--mode", default="persistent", choices=["waves", "persistent"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
     ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
     args = ap.parse_args()
@@ -411,12 +410,22 @@ def main():
     stack, k = device_stack(plan, w, torch, dev)
     stream = torch.cuda.current_stream()
 
-    def step(timed=False):
+    # one step = initial guess of every tile + all loops of the update
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(i=None):
         plan.load_tiles(stack, k)
-        plan.reconstruct(w.iters, mode=args.mode, graph=True, timed=timed and args.mode == "waves")
+        if i is not None:
+            ev[i][0].record(stream)
+        if args.mode == "persistent":
+            plan.reconstruct(w.iters, mode="persistent", graph=True)
+        else:
+            plan.reconstruct(w.iters, mode="waves", graph=True, timed=True)
+        if i is not None:
+            ev[i][1].record(stream)
 
     for _ in range(max(args.warmup, 1)):
-        step(timed=True)
+        step()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -427,8 +436,8 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step(timed=True)
+    for i in range(args.steps):
+        step(i)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -436,28 +445,28 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     st = plan.stats()
+    run_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms, _, value = aggregate(ms, w.updates * args.steps, dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
     launches = (st["load_launches"] + st["run_launches"]) * args.steps
 
-    # roofline of the fused update kernel from the event-timed launches of the last step
+    # roofline of the dominant kernel, from the CUDA events of the timed region
     fpu, bpu = flops_per_update(w), bytes_per_update(w)
-    roof = None
-    if st["update_ms"] > 0:
+    if args.mode == "persistent":
+        per_launch_s, upl, kname, n_launch = run_ms / 1e3, w.updates, "fpm::persistent_kernel", 1
+        share = run_ms / ms_per_step
+    else:
         per_launch_s = st["update_ms"] / 1e3 / st["update_launches"]
-        upl = st["updates"] / st["update_launches"]
-        achieved = fpu * upl / per_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": (TRAFFIC_PER_UPDATE[w.tile] * upl if w.tile in TRAFFIC_PER_UPDATE else None),
-                "traffic_source": "ncu dram__bytes_read+write of a 9-update launch (3x3 tiles of 256), "
-                                  "scaled to the average launch's updates",
-                "kernel": "fpm::update_kernel", "launches_per_step": st["update_launches"],
-                "updates_per_launch": upl, "avg_launch_us": per_launch_s * 1e6,
-                "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
-                "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9,
-                "update_kernel_share": st["update_ms"] / ms_per_step,
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (max SM clock)"}
+        upl, kname, n_launch = st["updates"] / st["update_launches"], "fpm::update_kernel", st["update_launches"]
+        share = st["update_ms"] / ms_per_step
+    achieved = fpu * upl / per_launch_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": (TRAFFIC_PER_UPDATE[w.tile] * upl if w.tile in TRAFFIC_PER_UPDATE else None),
+            "kernel": kname, "launches_per_step": n_launch, "updates_per_launch": upl,
+            "avg_launch_us": per_launch_s * 1e6, "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
+            "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9, "kernel_share_of_step": share,
+            "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz (max SM clock); no measured FP32 peak"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -465,6 +474,7 @@ def main():
             "config": {"workload": w.name, "sensor": w.sensor, "tile": w.tile, "hr": w.hr, "tiles": w.n_tiles,
                        "leds": w.n_leds, "iters": w.iters, "epry": w.epry, "updates_per_step": w.updates,
                        "mode": args.mode + "+graph", "ms_per_fov": ms_per_step,
+                       "clusters": st["persistent_clusters"] if args.mode == "persistent" else None,
                        "l2": "inputs larger than L2 (1.9 GB stack, 0.5 GB spectra); no flush",
                        "parallelism": f"{world} independent FOV replicas" if world > 1 else "1 GPU"},
             "roofline": roof, "gpu_launches": launches, "clocks": clk}
@@ -503,19 +513,28 @@ def main():
         line["plain_path"] = {"value": plain_upd / plain_s, "unit": UNIT,
                               "sample": f"one loop of all {w.n_tiles} tiles ({plain_upd} updates), no graph",
                               "speedup_of_batched": value / (plain_upd / plain_s)}
-        # the same FOV step in persistent mode (one launch per step, graph)
+        # the same FOV step in the other execution mode
+        other = "waves" if args.mode == "persistent" else "persistent"
         plan.load_tiles(stack, k)
-        plan.reconstruct(w.iters, mode="persistent", graph=True)
+        plan.reconstruct(w.iters, mode=other, graph=True, timed=other == "waves")
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
             plan.load_tiles(stack, k)
-            plan.reconstruct(w.iters, mode="persistent", graph=True)
+            plan.reconstruct(w.iters, mode=other, graph=True, timed=other == "waves")
         e1.record(stream)
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / args.steps
-        line["persistent_path"] = {"value": w.updates / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                                   "clusters": plan.stats()["persistent_clusters"]}
+        alt = {"value": w.updates / (pms / 1e3), "unit": UNIT, "ms_per_step": pms}
+        if other == "waves":
+            s2 = plan.stats()
+            t_l = s2["update_ms"] / 1e3 / s2["update_launches"]
+            u_l = s2["updates"] / s2["update_launches"]
+            alt["update_kernel"] = {"avg_launch_us": t_l * 1e6, "updates_per_launch": u_l,
+                                    "achieved_tflops": fpu * u_l / t_l / 1e12,
+                                    "frac": fpu * u_l / t_l / 1e12 / FP32_PEAK_TFLOPS,
+                                    "share_of_step": s2["update_ms"] / pms}
+        line[other + "_path"] = alt
         del host_stack, host_out
         line["uneven_batch"] = uneven_batch(torch, dev)
         if args.serving_jobs > 0:

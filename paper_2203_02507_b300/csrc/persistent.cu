@@ -104,7 +104,9 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
   }
 }
 
-template <typename Img>
+// MSEL = 0: any tile side (dispatch per entry); MSEL = m: every job has tile side m,
+// so the kernel carries only that variant (and its register needs).
+template <typename Img, int MSEL>
 __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constant__ PersistArgs pa) {
   extern __shared__ float4 smem_raw[];
   __shared__ int s_idx, s_flag;
@@ -135,11 +137,21 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
     const JobArgs ja = pa.jobs[it.job];
     const int4 item = make_int4(it.ltile, it.led, it.slot, 0);
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
-    switch (ja.m) {
-      case 64: run_update<P64, Img>(ja.u, item, smem); break;
-      case 128: run_update<P128, Img>(ja.u, item, smem); break;
-      case 192: run_update<P192, Img>(ja.u, item, smem); break;
-      default: run_update<P256, Img>(ja.u, item, smem); break;
+    if constexpr (MSEL == 64) {
+      run_update<P64, Img>(ja.u, item, smem);
+    } else if constexpr (MSEL == 128) {
+      run_update<P128, Img>(ja.u, item, smem);
+    } else if constexpr (MSEL == 192) {
+      run_update<P192, Img>(ja.u, item, smem);
+    } else if constexpr (MSEL == 256) {
+      run_update<P256, Img>(ja.u, item, smem);
+    } else {
+      switch (ja.m) {
+        case 64: run_update<P64, Img>(ja.u, item, smem); break;
+        case 128: run_update<P128, Img>(ja.u, item, smem); break;
+        case 192: run_update<P192, Img>(ja.u, item, smem); break;
+        default: run_update<P256, Img>(ja.u, item, smem); break;
+      }
     }
     // run_update ends with a cluster barrier: all of this update's writes are issued
     if (leader) {
@@ -220,6 +232,7 @@ struct QueueDev {
   int n_items = 0, n_tiles = 0, n_jobs = 0;
   size_t smem = 0;
   int dtype = FPM_U16;
+  int msel = 0;                   // common tile side of the jobs, 0 if mixed
 };
 
 void free_queue(QueueDev *q) {
@@ -252,8 +265,10 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
   const int dtype = plan_image_dtype(jobs[0].plan);
   std::vector<JobArgs> ja(jobs.size());
   size_t smem = 0;
+  int msel = jobs[0].plan->m;
   for (size_t j = 0; j < jobs.size(); ++j) {
     fpm_plan *p = jobs[j].plan;
+    if (p->m != msel) msel = 0;
     if (plan_image_dtype(p) != dtype) return fail(FPM_EINVAL, "jobs of one persistent run must share the image type");
     std::memset(&ja[j], 0, sizeof(JobArgs));
     ja[j].u = plan_update_args(p);
@@ -273,6 +288,7 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
   q->n_jobs = (int)jobs.size();
   q->smem = smem;
   q->dtype = dtype;
+  q->msel = msel;
   return FPM_OK;
 }
 
@@ -307,7 +323,16 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   pa.merged = q->counters + 1 + q->n_tiles;
   pa.err = err;
   pa.timeout_ns = stall_test ? 50000000LL : 2000000000LL;   // 50 ms for the test hook, else 2 s
-  void (*k)(PersistArgs) = q->dtype == FPM_U16 ? &persistent_kernel<uint16_t> : &persistent_kernel<float>;
+  using K = void (*)(PersistArgs);
+  const bool u16 = q->dtype == FPM_U16;
+  K k;
+  switch (q->msel) {
+    case 64: k = u16 ? (K)&persistent_kernel<uint16_t, 64> : (K)&persistent_kernel<float, 64>; break;
+    case 128: k = u16 ? (K)&persistent_kernel<uint16_t, 128> : (K)&persistent_kernel<float, 128>; break;
+    case 192: k = u16 ? (K)&persistent_kernel<uint16_t, 192> : (K)&persistent_kernel<float, 192>; break;
+    case 256: k = u16 ? (K)&persistent_kernel<uint16_t, 256> : (K)&persistent_kernel<float, 256>; break;
+    default: k = u16 ? (K)&persistent_kernel<uint16_t, 0> : (K)&persistent_kernel<float, 0>; break;
+  }
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));
   cudaLaunchConfig_t cfg{};
   cfg.blockDim = dim3(kPT, 1, 1);

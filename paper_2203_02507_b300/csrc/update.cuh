@@ -38,10 +38,13 @@ namespace cg = cooperative_groups;
 namespace fpm {
 
 
-// Swizzled position of (row i, local column p) in "inter" (row length W):
-// consecutive rows of one column and columns 16 apart within one row fall in
-// different banks.
-__device__ __forceinline__ int inter_at(int i, int p, int w) { return i * w + (p ^ ((i ^ (p >> 4)) & 15)); }
+// Swizzled position in "inter" (row length W) of local column p of stored row i,
+// which holds box row y: consecutive rows of one column and columns 16 apart
+// within one row fall in different banks.  The swizzle depends on y mod 16 only
+// through its low bits, so a lane that walks rows y = B a + b (B a multiple of
+// 8) keeps a constant or two-valued swizzle.
+__device__ __forceinline__ int inter_swz(int y, int p) { return p ^ ((y ^ (p >> 4)) & 15); }
+__device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz(y, p); }
 
 template <typename Img>
 __device__ __forceinline__ float load_image(const Img *img, long long off) {
@@ -164,7 +167,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = k1 + A * k2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          inter_of[owner][inter_at(i, p, W)] = v[k2];
+          inter_of[owner][inter_at(i, by, p, W)] = v[k2];
         }
       }
     }
@@ -182,27 +185,49 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 
   // ---- phase 2: columns: IDFT along y, amplitude step, DFT along y ---------
   const int y_lo = a.y_lo, y_hi = a.y_lo + rows - 1;
-  for (int c = g; c < W; c += G) {
-    const int x = q * W + c;
-    // this lane's measured pixels for the amplitude step (rows y = k1 + A k2), fetched early
-    float meas[Cfg::UB][B];
+  // per lane: which rows y = B a + b (first pass) and y = kk + B k2 (last pass) are stored
+  unsigned in_mask[Cfg::UA], out_mask[Cfg::UA];
+#pragma unroll
+  for (int u = 0; u < Cfg::UA; ++u) {
+    const int b = tl + u * TPT;
+    in_mask[u] = 0;
+    out_mask[u] = 0;
+#pragma unroll
+    for (int aa = 0; aa < A; ++aa) {
+      const int y = B * aa + b;
+      if (b < B && y >= y_lo && y <= y_hi) in_mask[u] |= 1u << aa;
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < A; ++k2) {
+      const int y = b + B * k2;
+      if (b < B && y >= y_lo && y <= y_hi) out_mask[u] |= 1u << k2;
+    }
+  }
+  // measured pixels of this lane's rows y = k1 + A k2, one column ahead
+  float meas[Cfg::UB][B];
+  auto fetch = [&](int col, float (&dst)[Cfg::UB][B]) {
 #pragma unroll
     for (int u = 0; u < Cfg::UB; ++u) {
       const int k1 = tl + u * TPT;
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2)
-        meas[u][k2] = (k1 < A) ? load_image<Img>(img, (long long)(k1 + A * k2) * a.stride_row + x) : 0.f;
+        dst[u][k2] = (k1 < A && col < W) ? load_image<Img>(img, (long long)(k1 + A * k2) * a.stride_row + q * W + col)
+                                         : 0.f;
     }
+  };
+  fetch(g, meas);
+  for (int c = g; c < W; c += G) {
+    float next[Cfg::UB][B];
+    fetch(c + G, next);
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int b = tl + u * TPT;
       if (b < B) {
         float2 v[A];
+        const float2 *col_base = inter + (b - y_lo) * W;   // row y = B aa + b is stored at i = y - y_lo
 #pragma unroll
-        for (int aa = 0; aa < A; ++aa) {
-          const int y = B * aa + b;
-          v[aa] = (y >= y_lo && y <= y_hi) ? inter[inter_at(y - y_lo, c, W)] : make_float2(0.f, 0.f);
-        }
+        for (int aa = 0; aa < A; ++aa)
+          v[aa] = ((in_mask[u] >> aa) & 1u) ? col_base[aa * B * W + inter_swz(B * aa + b, c)] : make_float2(0.f, 0.f);
         Dft<A, 1>::run(v);
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], twi[k1 * B + b]);
@@ -225,7 +250,12 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const float2 f = v[k2];
           const float m2 = cabs2(f);
           if (m2 > 0.f) {
-            const float s = (in > 0.f) ? __fmul_rn(in, rsqrtf(__fmul_rn(in, m2))) : 0.f;
+            // sqrt(I) / |phi~| = I / sqrt(I |phi~|^2); the hardware reciprocal square root
+            // is refined by one Newton-Raphson step, r += r (1 - x r^2) / 2
+            const float x = __fmul_rn(in, m2);
+            float r = rsqrtf(x);
+            r = __fmaf_rn(__fmul_rn(0.5f, r), __fmaf_rn(-__fmul_rn(x, r), r, 1.0f), r);
+            const float s = (in > 0.f) ? __fmul_rn(in, r) : 0.f;
             v[k2] = cscale(f, s);
           } else {
             v[k2] = make_float2(sqrtf(in), 0.f);
@@ -254,14 +284,17 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
         for (int bb = 0; bb < A; ++bb) v[bb] = scr[bb * (B + 1) + kk];
         Dft<A, -1>::run(v);
+        float2 *col_base = inter + (kk - y_lo) * W;
 #pragma unroll
-        for (int k2 = 0; k2 < A; ++k2) {
-          const int y = kk + B * k2;
-          if (y >= y_lo && y <= y_hi) inter[inter_at(y - y_lo, c, W)] = v[k2];
-        }
+        for (int k2 = 0; k2 < A; ++k2)
+          if ((out_mask[u] >> k2) & 1u) col_base[k2 * B * W + inter_swz(kk + B * k2, c)] = v[k2];
       }
     }
     __syncwarp(gmask);
+#pragma unroll
+    for (int u = 0; u < Cfg::UB; ++u)
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) meas[u][k2] = next[u][k2];
   }
   if constexpr (C > 1) {
     cg::this_cluster().sync();
@@ -320,7 +353,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = A * aa + b2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          v[aa] = inter_of[owner][inter_at(i, p, W)];
+          v[aa] = inter_of[owner][inter_at(i, by, p, W)];
         }
         Dft<B, -1>::run(v);
 #pragma unroll
