@@ -100,60 +100,51 @@ static __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, i
   }
 }
 
-// Add the wave's pupil corrections in slot (= sequence) order and compute
-// max |P|^2 over the support.  The support rows are cut into kNormParts
-// chunks; chunk c of tile t writes its maximum to pnorm_part[t][c] and readers
-// take the max of the kNormParts values, so the result does not depend on
-// scheduling.  merge_chunk is one chunk done by one whole CTA.
-__device__ __forceinline__ void merge_chunk(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
-                                            float *__restrict__ pnorm_part, const int2 *__restrict__ chords, int t,
-                                            int ns, int chunk, int y_lo, int rows, int m, int slots) {
-  const int rpp = (rows + kNormParts - 1) / kNormParts;
-  const int r0 = chunk * rpp, r1 = min(rows, r0 + rpp);
-  const size_t mm = (size_t)m * m;
-  float2 *p = pup + (size_t)t * mm;
-  float mx = 0.f;
-  for (int idx = threadIdx.x; idx < (r1 - r0) * m; idx += blockDim.x) {
-    const int by = y_lo + r0 + idx / m, bx = idx % m;
+// Close a wave of a tile: add its ns pupil corrections to the pupil in slot
+// (= sequence) order.  Corrections are zero off the support (the update writes
+// them only there and they start zeroed) and so is the pupil, so whole aligned
+// pixel pairs of each support row's chord are summed with 16-byte loads, all
+// of a pair's corrections in flight together.  Rows are cut into `parts`
+// chunks; merge_rows does chunk `part` with the threads [t0, t0 + nt) of the
+// calling CTA(s).
+constexpr int kMergeSlots = 8;   // corrections loaded together
+
+__device__ __forceinline__ void merge_rows(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
+                                           const int2 *__restrict__ chords, int t, int ns, int part, int parts,
+                                           int y_lo, int rows, int m, int slots, int t0, int nt) {
+  if (ns <= 0) return;
+  const int rpp = (rows + parts - 1) / parts;
+  const int r0 = part * rpp, r1 = min(rows, r0 + rpp);
+  const int hp = m / 2;                                   // pixel pairs per row
+  const size_t mm2 = (size_t)m * m / 2;                   // float4 per pupil
+  float4 *p = reinterpret_cast<float4 *>(pup + (size_t)t * m * m);
+  const float4 *d = reinterpret_cast<const float4 *>(dpup + (size_t)t * slots * m * m);
+  for (int idx = t0; idx < (r1 - r0) * hp; idx += nt) {
+    const int by = y_lo + r0 + idx / hp, pr = idx % hp;
     const int2 ch = chords[by];
-    if (bx < ch.x || bx > ch.y) continue;
-    const size_t off = (size_t)by * m + bx;
-    float2 v = p[off];
-    if (ns > 0) {
-      const float2 *d = dpup + (size_t)t * slots * mm + off;
-      int s = 0;
-      for (; s + 4 <= ns; s += 4) {
-        const float2 a0 = d[(size_t)s * mm], a1 = d[(size_t)(s + 1) * mm];
-        const float2 a2 = d[(size_t)(s + 2) * mm], a3 = d[(size_t)(s + 3) * mm];
-        v = cadd(cadd(cadd(cadd(v, a0), a1), a2), a3);
-      }
-      for (; s < ns; ++s) v = cadd(v, d[(size_t)s * mm]);
-      p[off] = v;
+    if (2 * pr + 1 < ch.x || 2 * pr > ch.y) continue;
+    const size_t off = (size_t)by * hp + pr;
+    float4 v = p[off];
+    for (int s0 = 0; s0 < ns; s0 += kMergeSlots) {
+      float4 a[kMergeSlots];
+#pragma unroll
+      for (int k = 0; k < kMergeSlots; ++k)
+        a[k] = (s0 + k < ns) ? d[(size_t)(s0 + k) * mm2 + off] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < kMergeSlots; ++k)
+        if (s0 + k < ns) v = make_float4(v.x + a[k].x, v.y + a[k].y, v.z + a[k].z, v.w + a[k].w);
     }
-    mx = fmaxf(mx, cabs2(v));
-  }
-  __shared__ float red[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __syncthreads();                       // red may still be read by a previous call
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float v = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) pnorm_part[(size_t)t * kNormParts + chunk] = v;
+    p[off] = v;
   }
 }
 
-// Grid: (merge entries (tile, slots), kNormParts chunks).
+// Grid: (entries (tile, slots), kNormParts row chunks).
 static __global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
-                                                           float *__restrict__ pnorm_part,
-                                                           const int2 *__restrict__ merges,
+                                                           const int2 *__restrict__ entries,
                                                            const int2 *__restrict__ chords, int y_lo, int rows, int m,
                                                            int slots) {
-  const int2 mg = merges[blockIdx.x];
-  merge_chunk(pup, dpup, pnorm_part, chords, mg.x, mg.y, blockIdx.y, y_lo, rows, m, slots);
+  const int2 e = entries[blockIdx.x];
+  merge_rows(pup, dpup, chords, e.x, e.y, blockIdx.y, kNormParts, y_lo, rows, m, slots, threadIdx.x, blockDim.x);
 }
 
 // Simulator: box of the unshifted DFT spectrum times the pupil, placed in

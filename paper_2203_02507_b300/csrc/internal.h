@@ -16,12 +16,14 @@ void clear_error();
 
 struct DeviceState;   // device-side buffers of a plan (runtime.cu)
 
-// Wave-step work lists of a plan's schedule, flattened for launches.
+// Wave-step work lists of a plan's schedule, flattened for launches.  Step s
+// holds wave s of every tile that has one.
 struct StepLists {
-  // item = (tile, led, slot, seq) ; items of step w are items[step_off[w] .. step_off[w+1])
+  // item = (tile, led, slot, sequence index); items of step s are
+  // items[step_off[s] .. step_off[s+1]), sorted by tile
   std::vector<int32_t> items;       // 4 ints per item
   std::vector<int64_t> step_off;    // [n_steps + 1]
-  // merges of step w: (tile, n_slots) pairs in merge[merge_off[w] .. merge_off[w+1])
+  // merges of step s: (tile, n_slots) in merges[merge_off[s] .. merge_off[s+1])
   std::vector<int32_t> merges;      // 2 ints per entry
   std::vector<int64_t> merge_off;   // [n_steps + 1]
   int32_t n_steps = 0;

@@ -6,8 +6,8 @@
 // device synchronisation that cudaMalloc/cudaFree can imply) would stall the
 // camera.  fpm_update_tile_static serves them: the caller passes the spectrum,
 // the pupil and the measured image, and every temporary the update needs (the
-// pupil correction, the normaliser partials, the support chords, the twiddle
-// tables and the one-item work list) lives in the file-scope array below.
+// pupil correction, the support chords, the twiddle tables, the one-item work
+// list and the merge entry) lives in the file-scope array below.
 //
 // The array is a fixed 1 MiB per device that loads this library, held until
 // the process exits.  All calls on a device share it and it keeps the last
@@ -74,12 +74,11 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   if (m < 16 || m > 4096 || m % 16) return fail(FPM_EINVAL, "tile side %d out of range", m);
   if (n < 2 * m || n > 8 * m || n % m)
     return fail(FPM_EINVAL, "HR side %d must be 2..8 times the tile side %d", n, m);
-  // layout of the static array: [pupil correction m*m][partial maxima][tables]
+  // layout of the static array: [pupil correction m*m][tables]
   const size_t dp_bytes = (size_t)m * m * sizeof(float2);
-  const size_t norm_off = fpm::align256(dp_bytes);
-  const size_t blob_off = norm_off + 256;
+  const size_t blob_off = fpm::align256(dp_bytes);
   const size_t chords_b = (size_t)m * sizeof(int2), tw_b = (size_t)m * sizeof(float2);
-  const size_t blob_bytes = chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + 2 * sizeof(int2);
+  const size_t blob_bytes = chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + sizeof(int2);
   const size_t need = blob_off + blob_bytes;
   if (need > fpm::kStaticScratchBytes)
     return fail(FPM_EINVAL, "tile side %d needs %zu bytes of static scratch; the limit is %zu", m, need,
@@ -121,13 +120,11 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   fpm::update_twiddles(m, fa, fb, twi, twf);
   w += 2 * tw_b;
   int4 *item = reinterpret_cast<int4 *>(w);
-  *item = make_int4(0, 0, 0, 0);
+  *item = make_int4(0, 0, 0, 0);         // tile 0, LED 0, slot 0
   int2 *sh = reinterpret_cast<int2 *>(item + 1);
   sh[0] = make_int2(shift_y, shift_x);   // shift of LED 0
   sh[1] = make_int2(0, 0);               // origin of tile 0 in the image
-  int2 *mg = sh + 2;
-  mg[0] = make_int2(0, 0);               // normaliser only
-  mg[1] = make_int2(0, 1);               // add one correction, then normaliser
+  sh[2] = make_int2(0, 1);               // merge entry: tile 0, one correction
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dev + blob_off, blob, blob_bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(FPM_ECUDA, "copy of the update tables: %s", cudaGetErrorString(e));
@@ -139,16 +136,18 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   const int2 *d_sh = reinterpret_cast<const int2 *>(d_item + 1);
   const int2 *d_mg = d_sh + 2;
   float2 *d_dp = reinterpret_cast<float2 *>(dev);
-  float *d_norm = reinterpret_cast<float *>(dev + norm_off);
   float2 *pup = static_cast<float2 *>(pupil);
 
-  // 1. max |P|^2 of the current pupil  2. the update  3. (EPRY) add its correction
-  if ((rc = fpm::launch_merge(pup, d_dp, d_norm, d_mg, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
+  // 1. zero the correction (the merge sums whole pixel pairs, so entries off this
+  //    call's support must be zero)  2. the update  3. (EPRY) add the correction
+  if (epry) {
+    e = cudaMemsetAsync(d_dp, 0, dp_bytes, st);
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "clearing the static correction: %s", cudaGetErrorString(e));
+  }
   fpm::UpdateArgs a{};
   a.spec = static_cast<float2 *>(spectrum);
   a.pup = pup;
   a.dpup = epry ? d_dp : nullptr;
-  a.pnorm = d_norm;
   a.items = d_item;
   a.shifts = d_sh;
   a.origins = d_sh + 1;
@@ -167,6 +166,6 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   a.slots = 1;
   a.err = nullptr;
   if ((rc = fpm::launch_update_items(m, rows, FPM_F32, a, 0, 1, st))) return rc;
-  if (epry && (rc = fpm::launch_merge(pup, d_dp, d_norm, d_mg + 1, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
+  if (epry && (rc = fpm::launch_merge(pup, d_dp, d_mg, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
   return FPM_OK;
 }

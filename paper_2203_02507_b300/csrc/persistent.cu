@@ -7,8 +7,9 @@
 // until the entry's tile has finished and merged its previous wave (Sec. 3.2:
 // an update may start once the updates it depends on are done), runs the fused
 // update, and counts itself done on its tile.  The cluster that completes a
-// tile's wave adds the wave's pupil corrections in sequence order, recomputes
-// the max|P|^2 partials, and releases the next wave.  Entries are claimed in
+// tile's wave adds the wave's pupil corrections in sequence order (both CTAs,
+// 16-byte loads, every correction of a pixel pair in flight) and releases the
+// next wave.  Entries are claimed in
 // queue order and depend only on earlier entries, which are held by running
 // clusters, so the queue cannot deadlock.  Every wait is bounded (a global
 // timer); a wait that runs out sets an error code and an abort flag that ends
@@ -163,9 +164,9 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
     cl.sync();
     if (s_flag) {          // this cluster completed the tile's wave: merge it, release the next
       if (ja.epry)
-        for (int c = (int)q; c < kNormParts; c += kPC)
-          merge_chunk(const_cast<float2 *>(ja.u.pup), ja.u.dpup, const_cast<float *>(ja.u.pnorm), ja.u.chords,
-                      it.ltile, it.width, c, ja.u.y_lo, ja.u.rows, ja.m, ja.u.slots);
+        merge_rows(const_cast<float2 *>(ja.u.pup), ja.u.dpup, ja.u.chords, it.ltile, it.width, (int)q, kPC,
+                   ja.u.y_lo, ja.u.rows, ja.m, ja.u.slots, threadIdx.x, blockDim.x);
+      __threadfence();
       cl.sync();
       if (leader) {
         __threadfence();

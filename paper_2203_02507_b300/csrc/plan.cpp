@@ -251,7 +251,6 @@ const StepLists &step_lists(fpm_plan *p, int32_t iters) {
   sl.step_off = per_step;
   sl.items.assign((size_t)per_step[steps] * 4, 0);
   std::vector<int64_t> fill(per_step.begin(), per_step.end() - 1);
-  sl.merge_off.assign(steps + 1, 0);
   std::vector<std::vector<int32_t>> merge_step(steps);
   std::vector<int32_t> slot(steps, 0);
   for (int t = 0; t < T; ++t) {
@@ -271,6 +270,7 @@ const StepLists &step_lists(fpm_plan *p, int32_t iters) {
         merge_step[s].push_back(slot[s]);
       }
   }
+  sl.merge_off.assign(steps + 1, 0);
   for (int s = 0; s < steps; ++s) {
     sl.merge_off[s + 1] = sl.merge_off[s] + (int64_t)merge_step[s].size() / 2;
     sl.merges.insert(sl.merges.end(), merge_step[s].begin(), merge_step[s].end());

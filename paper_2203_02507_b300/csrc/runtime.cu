@@ -146,7 +146,7 @@ struct DeviceBuf {
 struct StepDev {
   int32_t iters = 0;
   int4 *items = nullptr;
-  int2 *merges = nullptr;
+  int2 *merges = nullptr;         // (tile, slots) per step, see StepLists
 };
 
 struct GraphKey {
@@ -159,12 +159,11 @@ struct GraphKey {
 
 struct DeviceState {
   int device = -1;
-  float2 *spec = nullptr, *pup = nullptr, *dpup = nullptr;
-  float *pnorm = nullptr;
+  float2 *spec = nullptr, *pup = nullptr, *dpup = nullptr;   // pup: [T][m][m]; dpup: [T][W][m][m]
   int2 *shifts = nullptr, *origins = nullptr, *chords = nullptr;
   float2 *tw_inv = nullptr, *tw_fwd = nullptr;      // update kernel split
   float2 *twl_fwd_m = nullptr;                      // line FFT tables
-  int2 *norm_all = nullptr;                         // (t, 0) for every tile
+
   unsigned *err = nullptr;
   void *stack_owned = nullptr;
   size_t stack_owned_bytes = 0;
@@ -208,9 +207,9 @@ void destroy_device_state(fpm_plan *p) {
     dfree(s.items);
     dfree(s.merges);
   }
-  for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->pnorm, (void *)d->shifts,
-                  (void *)d->origins, (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd,
-                  (void *)d->twl_fwd_m, (void *)d->norm_all, (void *)d->err, d->stack_owned})
+  for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
+                  (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
+                  d->stack_owned})
     dfree(q);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -235,25 +234,24 @@ static int ensure_device_state(fpm_plan *p) {
   const size_t T = p->n_tiles, n = p->n, m = p->m;
   cudaError_t e;
   if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d->pnorm, T * kNormParts * sizeof(float))) != cudaSuccess)
+      (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess)
     return fail(FPM_ENOMEM, "device allocation of the tile state failed: %s", cudaGetErrorString(e));
   if (p->epry) {
-    if ((e = cudaMalloc((void **)&d->dpup, T * (size_t)p->max_width * m * m * sizeof(float2))) != cudaSuccess)
+    const size_t db = T * (size_t)p->max_width * m * m * sizeof(float2);
+    if ((e = cudaMalloc((void **)&d->dpup, db)) != cudaSuccess)
       return fail(FPM_ENOMEM, "device allocation of the pupil corrections failed: %s", cudaGetErrorString(e));
+    FPM_CK(cudaMemset(d->dpup, 0, db));   // the merge sums whole pixel pairs: off-support entries stay zero
   }
-  std::vector<int2> sh((size_t)p->n_tiles * p->n_leds), org(p->n_tiles), ch(p->m), norm(p->n_tiles);
+  std::vector<int2> sh((size_t)p->n_tiles * p->n_leds), org(p->n_tiles), ch(p->m);
   for (size_t i = 0; i < sh.size(); ++i) sh[i] = make_int2(p->shifts[i * 2], p->shifts[i * 2 + 1]);
   for (int t = 0; t < p->n_tiles; ++t) {
     org[t] = make_int2(p->origins[t * 2], p->origins[t * 2 + 1]);
-    norm[t] = make_int2(t, 0);
   }
   for (int i = 0; i < p->m; ++i) ch[i] = make_int2(p->chord_lo[i], p->chord_hi[i]);
   int rc;
   if ((rc = upload(&d->shifts, sh.data(), sh.size() * sizeof(int2)))) return rc;
   if ((rc = upload(&d->origins, org.data(), org.size() * sizeof(int2)))) return rc;
   if ((rc = upload(&d->chords, ch.data(), ch.size() * sizeof(int2)))) return rc;
-  if ((rc = upload(&d->norm_all, norm.data(), norm.size() * sizeof(int2)))) return rc;
   std::vector<float2> ti(p->m), tf(p->m);
   update_twiddles(p->m, d->var->a, d->var->b, ti.data(), tf.data());
   if ((rc = upload(&d->tw_inv, ti.data(), ti.size() * sizeof(float2)))) return rc;
@@ -324,12 +322,9 @@ static int run_init(fpm_plan *p, cudaStream_t st) {
   init_place_kernel<<<grid_for(tot, 256), 256, 0, st>>>(d->spec, tmp, m, n, T, scale);
   FPM_CK(cudaGetLastError());
   FPM_CK(cudaFreeAsync(tmp, st));
-  // pupils and their normaliser
+  // pupils into buffer 0
   FPM_CK(cudaMemcpyAsync(d->pup, p->pupil0.data(), (size_t)T * m * m * sizeof(float2), cudaMemcpyHostToDevice, st));
-  merge_kernel<<<dim3(T, kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all, d->chords, p->y_lo,
-                                                     p->y_hi - p->y_lo + 1, m, p->max_width);
-  FPM_CK(cudaGetLastError());
-  d->load_launches = 5;   // gather, 2 x line FFT, place, normaliser
+  d->load_launches = 4;   // gather, 2 x line FFT, place
   return FPM_OK;
 }
 
@@ -353,7 +348,6 @@ static UpdateArgs make_args(fpm_plan *p, const StepDev *sd) {
   a.spec = d->spec;
   a.pup = d->pup;
   a.dpup = p->epry ? d->dpup : nullptr;
-  a.pnorm = d->pnorm;
   a.items = sd ? sd->items : nullptr;
   a.shifts = d->shifts;
   a.origins = d->origins;
@@ -419,11 +413,10 @@ int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long lo
   return FPM_OK;
 }
 
-int launch_merge(float2 *pup, const float2 *dpup, float *pnorm_part, const int2 *merges, int count,
-                 const int2 *chords, int y_lo, int rows, int m, int slots, cudaStream_t st) {
+int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, const int2 *chords, int y_lo,
+                 int rows, int m, int slots, cudaStream_t st) {
   if (count <= 0) return FPM_OK;
-  merge_kernel<<<dim3((unsigned)count, kNormParts), 256, 0, st>>>(pup, dpup, pnorm_part, merges, chords, y_lo, rows,
-                                                                   m, slots);
+  merge_kernel<<<dim3((unsigned)count, kNormParts), 256, 0, st>>>(pup, dpup, entries, chords, y_lo, rows, m, slots);
   FPM_CK(cudaGetLastError());
   return FPM_OK;
 }
@@ -471,13 +464,12 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
         d->timed_steps.push_back(s);
         d->timed_updates += i1 - i0;
       }
-      if (p->epry) {
+      if (p->epry) {   // close the wave: its corrections into the pupils, in sequence order
         const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
-        if (m1 > m0) {
-          merge_kernel<<<dim3((unsigned)(m1 - m0), kNormParts), 256, 0, st>>>(
-              d->pup, d->dpup, d->pnorm, sd->merges + m0, d->chords, p->y_lo, rows, p->m, p->max_width);
-          ++nl;
-        }
+        if ((rc = launch_merge(d->pup, d->dpup, sd->merges + m0, (int)(m1 - m0), d->chords, p->y_lo, rows, p->m,
+                               p->max_width, st)))
+          return rc;
+        if (m1 > m0) ++nl;
       }
     }
     FPM_CK(cudaGetLastError());
@@ -485,7 +477,7 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
     return FPM_OK;
   }
   if (mode == FPM_RUN_PLAIN) {
-    // one tile at a time, one LED per launch; the merges close every wave
+    // one tile at a time, one LED per launch
     for (int t = 0; t < p->n_tiles; ++t) {
       for (int s = 0; s < sl.n_steps; ++s) {
         const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
@@ -501,11 +493,11 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
           ++nl;
         }
         if (p->epry) {
-          const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
-          for (long long k = m0; k < m1; ++k)
+          for (long long k = sl.merge_off[s]; k < sl.merge_off[s + 1]; ++k)
             if (sl.merges[k * 2] == t) {
-              merge_kernel<<<dim3(1, kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, sd->merges + k,
-                                                                 d->chords, p->y_lo, rows, p->m, p->max_width);
+              if ((rc = launch_merge(d->pup, d->dpup, sd->merges + k, 1, d->chords, p->y_lo, rows, p->m,
+                                     p->max_width, st)))
+                return rc;
               ++nl;
             }
         }
@@ -763,7 +755,7 @@ int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device,
 
 size_t plan_device_bytes(const fpm_plan *p) {
   const size_t T = p->n_tiles, n = p->n, m = p->m;
-  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1) + T * kNormParts * 4;
+  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1);
 }
 
 }  // namespace fpm
@@ -904,14 +896,7 @@ int fpm_set_state(fpm_plan *p, int32_t tile, const void *spectrum, const void *p
   fpm::DeviceState *d = p->dev;
   const size_t nn = (size_t)p->n * p->n, mm = (size_t)p->m * p->m;
   if (spectrum) FPM_CK(cudaMemcpyAsync(d->spec + tile * nn, spectrum, nn * 8, cudaMemcpyHostToDevice, st));
-  if (pupil) {
-    FPM_CK(cudaMemcpyAsync(d->pup + tile * mm, pupil, mm * 8, cudaMemcpyHostToDevice, st));
-    // recompute the normaliser of this tile
-    fpm::merge_kernel<<<dim3(1, fpm::kNormParts), 256, 0, st>>>(d->pup, d->dpup, d->pnorm, d->norm_all + tile,
-                                                                d->chords, p->y_lo, p->y_hi - p->y_lo + 1, p->m,
-                                                                p->max_width);
-    FPM_CK(cudaGetLastError());
-  }
+  if (pupil) FPM_CK(cudaMemcpyAsync(d->pup + tile * mm, pupil, mm * 8, cudaMemcpyHostToDevice, st));
   FPM_CK(cudaStreamSynchronize(st));
   return FPM_OK;
 }

@@ -38,7 +38,7 @@ UpdateArgs plan_update_args(fpm_plan *p);
 int plan_image_dtype(const fpm_plan *p);
 // The plan's device error word ([0] code, [1] abort flag), or null.
 unsigned *plan_error_word(fpm_plan *p);
-// Launch the pupil merge / normaliser over `count` (tile, slots) entries.
-int launch_merge(float2 *pup, const float2 *dpup, float *pnorm_part, const int2 *merges, int count,
-                 const int2 *chords, int y_lo, int rows, int m, int slots, cudaStream_t st);
+// Launch the pupil merge over `count` (tile, slots) entries.
+int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, const int2 *chords, int y_lo,
+                 int rows, int m, int slots, cudaStream_t st);
 }  // namespace fpm

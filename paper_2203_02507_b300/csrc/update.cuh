@@ -9,6 +9,7 @@
 //   Phi' = (N/m)^2 DFT_m(phi')
 //   D    = Phi' - Phi
 //   O_box += conj(P) D / max|P|^2,  dP = conj(O_box_old) D / max|O_box_old|^2
+// Both maxima are reduced over the support inside the update.
 // The box is taken in its centred order: transforming a centred spectrum as if
 // it were in natural order multiplies the spatial field by (-1)^(x+y), which
 // the amplitude step preserves and the forward transform undoes, so no shift
@@ -66,6 +67,7 @@ struct UpdateCfg {
   static_assert(A * B == M, "m = A * B");
   static_assert(32 % TPT == 0 && T % 32 == 0, "groups must not straddle warps");
   static_assert(W % 16 == 0, "inter rows are swizzled in groups of 16");
+  static_assert(T <= 512, "the normaliser holds one partial per warp in 16 slots");
   // shared memory in bytes for R support rows
   static size_t smem_bytes(int rows) {
     return ((size_t)rows * W + (size_t)G * SCR + 2 * M) * sizeof(float2) + 64 * sizeof(float);
@@ -106,7 +108,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const int n = a.n;
   const int oy = n / 2 + sh.x - M / 2, ox = n / 2 + sh.y - M / 2;
   float2 *__restrict__ spec = a.spec + (size_t)tile * n * n + (size_t)oy * n + ox;   // box origin
-  const float2 *__restrict__ pup = a.pup + (size_t)tile * M * M;
+  const size_t mm = (size_t)M * M;
+  const float2 *__restrict__ pup = a.pup + (size_t)tile * mm;
+  float2 *dp_out = a.dpup ? a.dpup + ((size_t)tile * a.slots + slot) * mm : nullptr;
   const int2 org = a.origins[tile];
   const Img *img = reinterpret_cast<const Img *>(a.stack) + (long long)led * a.stride_led +
                    (long long)org.x * a.stride_row + org.y;
@@ -122,7 +126,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const int r0 = q * rpc, r1 = min(rows, r0 + rpc);
 
   // ---- phase 1: IDFT along x of every support row -------------------------
-  float omax = 0.f;
+  float omax = 0.f, pmax = 0.f;
   for (int i = r0 + g; i < r1; i += G) {
     const int by = a.y_lo + i;
     const int2 ch = a.chords[by];
@@ -143,6 +147,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) {
           omax = fmaxf(omax, cabs2(v[aa]));
+          pmax = fmaxf(pmax, cabs2(pv[aa]));
           v[aa] = cmul(v[aa], pv[aa]);
         }
         Dft<A, 1>::run(v);
@@ -173,10 +178,16 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
     }
     __syncwarp(gmask);
   }
-  // EPRY normaliser: max |O_box_old|^2 over the support, over the whole cluster
+  // normalisers: max |O_box_old|^2 and max |P|^2 over the support, over the whole cluster
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o));
-  if (lane == 0) red[tid >> 5] = omax;
+  for (int o = 16; o > 0; o >>= 1) {
+    omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+  }
+  if (lane == 0) {
+    red[tid >> 5] = omax;
+    red[16 + (tid >> 5)] = pmax;
+  }
   if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
@@ -303,26 +314,23 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   }
 
   // normalisers
-  float onorm = 0.f;
   if (tid < 32) {
-    float v = (tid < T / 32) ? red[tid] : 0.f;
+    const int wi = tid & 15;
+    float v = (wi < T / 32) ? red[tid] : 0.f;          // lanes 0-15: |O|^2, 16-31: |P|^2
     if constexpr (C > 1) {
       cg::cluster_group cl = cg::this_cluster();
       for (int r = 0; r < C; ++r)
-        if (r != q && tid < T / 32) v = fmaxf(v, cl.map_shared_rank(red, r)[tid]);
+        if (r != q && wi < T / 32) v = fmaxf(v, cl.map_shared_rank(red, r)[tid]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (tid == 0) red[32] = v;
+    if (tid == 16) red[33] = v;
   }
   __syncthreads();
-  onorm = red[32];
+  const float onorm = red[32], pn = red[33];
   const float inv_on = (onorm > 0.f) ? 1.f / onorm : 0.f;
-  float pn = 0.f;
-#pragma unroll
-  for (int k = 0; k < kNormParts; ++k) pn = fmaxf(pn, a.pnorm[(size_t)tile * kNormParts + k]);
   const float inv_pn = 1.f / pn;
-  float2 *dp = a.dpup ? a.dpup + ((size_t)tile * a.slots + slot) * M * M : nullptr;
 
   // ---- phase 3: DFT along x of the support rows, then the updates ----------
   for (int i = r0 + g; i < r1; i += G) {
@@ -379,9 +387,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
             const float2 d = csub(cscale(v[k2], a.scale), phi);
             const float2 pc = cmulc(d, p);        // D * conj(P)
             srow[x] = make_float2(__fmaf_rn(pc.x, inv_pn, o.x), __fmaf_rn(pc.y, inv_pn, o.y));
-            if (dp) {
+            if (dp_out) {
               const float2 oc = cmulc(d, o);      // D * conj(O_old)
-              dp[(size_t)by * M + x] = cscale(oc, inv_on);
+              dp_out[(size_t)by * M + x] = cscale(oc, inv_on);
             }
           }
         }

@@ -5,14 +5,13 @@
 
 namespace fpm {
 
-// Partial maxima per tile of max |P|^2 over the support (see merge_kernel).
+// Row chunks of the pupil merge (merge_kernel).
 constexpr int kNormParts = 8;
 
 struct UpdateArgs {
   float2 *spec;               // [T][N][N] centred spectra
-  const float2 *pup;          // [T][m][m] centred pupils
-  float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null
-  const float *pnorm;         // [T][kNormParts] partial maxima of |P|^2 over the support
+  const float2 *pup;          // [T][m][m] centred pupils (as of the update's wave start)
+  float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null; zero off the support
   const int4 *items;          // (tile, led, slot, sequence index)
   const int2 *shifts;         // [T][L] (sy, sx)
   const int2 *origins;        // [T] (y0, x0) on the sensor
@@ -27,7 +26,7 @@ struct UpdateArgs {
   int n_leds;
   int y_lo;                   // first support row (box coordinates)
   int rows;                   // R
-  int slots;                  // dP slots per tile
+  int slots;                  // correction slots per tile
   unsigned *err;
 };
 
