@@ -37,15 +37,23 @@ UNIT = "updates/s"
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
 
-# DRAM bytes per update of the update kernel (m -> bytes), from the latest ncu
-# capture in profiles/ of the kernel as it stands; a launch scales it by the
-# updates it processes.  Emptied whenever the kernel changes until re-captured.
-TRAFFIC_PER_UPDATE = {}
+# DRAM bytes per update ((mode, m) -> bytes) of the dominant kernel, from the
+# latest ncu capture in profiles/ of the kernel as it stands; a launch scales it
+# by the updates it processes.  Emptied whenever the kernel changes until
+# re-captured.
+TRAFFIC_PER_UPDATE = {
+    # profiles/persistent_kernel_m256_ncu_full.md: 527,265,024 + 91,071,488 B for 3,600 updates
+    ("persistent", 256): (527265024 + 91071488) / 3600,
+    # profiles/update_kernel_m256_ncu_full.md: 12,295,936 + 256 B for 32 updates
+    ("waves", 256): (12295936 + 256) / 32,
+}
 
 EXTRA = {
-    # small case of the same kernel for ncu captures: 3 x 3 tiles of 256, inputs > L2
+    # small cases of the same kernels for ncu captures (inputs larger than L2, well under a few GB)
     "ncu_m256": synth.Workload("ncu_m256", sensor=768, tile=256, tiles=3, overlap=16, iters=1, epry=True,
                                optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
+    "ncu16_m256": synth.Workload("ncu16_m256", sensor=1024, tile=256, tiles=4, overlap=16, iters=1, epry=True,
+                                 optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
 }
 
 
@@ -386,7 +394,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fov2048_m256")
-    ap.add_argument("--mode", default="persistent", choices=["waves", "persistent"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "waves", "persistent"],
+                    help="auto: fpm_autotune picks the fastest path on one loop of the data")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
     ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
     args = ap.parse_args()
@@ -409,6 +418,12 @@ def main():
     plan = plan_for(w)
     stack, k = device_stack(plan, w, torch, dev)
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.mode == "auto":
+        plan.load_tiles(stack, k)
+        entries, best = plan.autotune(iters=1)
+        tune = {"entries": entries, "best": best}
+        args.mode = entries[best]["mode"]
 
     # one step = initial guess of every tile + all loops of the update
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -462,7 +477,10 @@ def main():
     achieved = fpu * upl / per_launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": (TRAFFIC_PER_UPDATE[w.tile] * upl if w.tile in TRAFFIC_PER_UPDATE else None),
+            "traffic": (TRAFFIC_PER_UPDATE[(args.mode, w.tile)] * upl
+                        if (args.mode, w.tile) in TRAFFIC_PER_UPDATE else None),
+            "traffic_source": "ncu dram__bytes_read+write per update on a 16-tile case (profiles/), "
+                              "scaled by this launch's updates",
             "kernel": kname, "launches_per_step": n_launch, "updates_per_launch": upl,
             "avg_launch_us": per_launch_s * 1e6, "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
             "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9, "kernel_share_of_step": share,
@@ -473,7 +491,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "sensor": w.sensor, "tile": w.tile, "hr": w.hr, "tiles": w.n_tiles,
                        "leds": w.n_leds, "iters": w.iters, "epry": w.epry, "updates_per_step": w.updates,
-                       "mode": args.mode + "+graph", "ms_per_fov": ms_per_step,
+                       "mode": args.mode + "+graph", "ms_per_fov": ms_per_step, "autotune": tune,
                        "clusters": st["persistent_clusters"] if args.mode == "persistent" else None,
                        "l2": "inputs larger than L2 (1.9 GB stack, 0.5 GB spectra); no flush",
                        "parallelism": f"{world} independent FOV replicas" if world > 1 else "1 GPU"},

@@ -73,6 +73,7 @@ extern "C" {
 #define FPM_RUN_PLAIN      0  /* one tile at a time, one LED per launch          */
 #define FPM_RUN_WAVES      1  /* every tile's next wave in one launch            */
 #define FPM_RUN_PERSISTENT 2  /* one persistent kernel over a device work queue  */
+#define FPM_RUN_AUTO       3  /* the path fpm_autotune chose (persistent if none) */
 #define FPM_RUN_GRAPH      0x100 /* OR-able: replay the launches as a CUDA graph */
 #define FPM_RUN_TIMED      0x200 /* OR-able with FPM_RUN_WAVES: time each update
                                     launch with CUDA events (see fpm_get_stats)  */
@@ -250,6 +251,27 @@ typedef struct {
  * timed run happened.  Returns FPM_ETIMEOUT (with *out filled) when the last
  * persistent run's device wait gave up. */
 FPM_API int fpm_get_stats(fpm_plan *plan, fpm_stats *out);
+
+/* One candidate execution path and its measured time (fpm_autotune). */
+typedef struct {
+  int32_t mode;      /* FPM_RUN_WAVES or FPM_RUN_PERSISTENT                      */
+  int32_t threads;   /* threads per CTA of the update kernel                     */
+  int32_t cluster;   /* CTAs per update                                          */
+  double ms;         /* device time of `iters` loops on the plan's data          */
+} fpm_tune_entry;
+
+/*
+ * fpm_autotune -- time every execution path that fits the plan's tile side
+ * (wave-by-wave launches with each update-kernel variant -- threads per CTA,
+ * CTAs per SM -- and the persistent kernel) on `iters` loops of the plan's own
+ * loaded data, each replayed as a CUDA graph after a warm-up, and keep the
+ * fastest for FPM_RUN_AUTO and for FPM_RUN_WAVES.  The plan's spectra and pupils
+ * are saved first and restored afterwards.  entries (may be NULL) receives up
+ * to max_entries results, *n_entries their count, *best the chosen index.
+ * Synchronises the device.  FPM_ESTATE before fpm_load_tiles.
+ */
+FPM_API int fpm_autotune(fpm_plan *plan, int32_t iters, void *stream, fpm_tune_entry *entries, int32_t max_entries,
+                         int32_t *n_entries, int32_t *best);
 
 /* fpm_initial_pupil -- the plan's initial pupil of `tile` (host memory,
  * m x m centred complex64; host only, no CUDA call). */

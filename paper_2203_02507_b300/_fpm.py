@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EBUSY, ESTATE = 0, -1, -2, -3, -4,
 ORDER = {"center_out": 0, "raster": 1}
 EPRY = 1
 U16, F32 = 0, 1
-RUN = {"plain": 0, "waves": 1, "persistent": 2}
+RUN = {"plain": 0, "waves": 1, "persistent": 2, "auto": 3}
 RUN_GRAPH = 0x100
 RUN_TIMED = 0x200
 RUN_FAULT_TEST = 0x400
@@ -60,6 +60,10 @@ class PlanInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("threads", C.c_int32), ("cluster", C.c_int32), ("ms", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
                 ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
@@ -82,6 +86,7 @@ _SIGS = {
     "fpm_set_state": [_vp, _i32, _vp, _vp, _vp],
     "fpm_initial_pupil": [_vp, _i32, _vp],
     "fpm_get_stats": [_vp, C.POINTER(Stats)],
+    "fpm_autotune": [_vp, _i32, _vp, C.POINTER(TuneEntry), _i32, C.POINTER(_i32), C.POINTER(_i32)],
     "fpm_simulate": [_vp, _vp, _vp, _vp],
     "fpm_server_create": [C.c_size_t, C.POINTER(_vp)],
     "fpm_submit": [_vp, _vp, _i32, _vp, _i32, _i32, _i64, _i64, _f32, C.POINTER(_i64)],
@@ -208,6 +213,16 @@ class Plan:
         flag = (RUN[mode] | (RUN_GRAPH if graph else 0) | (RUN_TIMED if timed else 0)
                 | (RUN_FAULT_TEST if fault_test else 0))
         _check(_lib.fpm_reconstruct(self._h, int(iters or self.iters), flag, _stream(stream)))
+
+    def autotune(self, iters: int = 1, stream=None):
+        """Time every execution path on `iters` loops of the loaded data and keep the
+        fastest (for mode="auto"); returns ([{mode, threads, cluster, ms}], best index)."""
+        ent = (TuneEntry * 16)()
+        n, best = _i32(), _i32()
+        _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, 16, C.byref(n), C.byref(best)))
+        names = {v: k for k, v in RUN.items()}
+        out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "ms": e.ms} for e in ent[:n.value]]
+        return out, best.value
 
     def stats(self, check: bool = True) -> dict:
         st = Stats()

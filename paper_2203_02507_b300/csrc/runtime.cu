@@ -45,13 +45,17 @@ static Variant make_variant() {
 
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
 using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;
+using Cfg64w = UpdateCfg<64, 8, 8, 8, 1, 256, 2>;
 using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128, 2>;
+using Cfg128w = UpdateCfg<128, 16, 8, 8, 1, 256, 1>;
 using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256, 1>;
+using Cfg192c = UpdateCfg<192, 12, 16, 16, 2, 256, 1>;
 using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 
 static const std::vector<Variant> &variants() {
-  static const std::vector<Variant> v = {make_variant<Cfg64>(), make_variant<Cfg128>(), make_variant<Cfg192>(),
+  static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),
+                                         make_variant<Cfg128w>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),
                                          make_variant<Cfg256w>(), make_variant<Cfg256>()};
   return v;
 }
@@ -184,6 +188,7 @@ struct DeviceState {
   bool timed_valid = false;
   std::map<int32_t, QueueDev *> queues;        // persistent queues by loop count
   int persistent_clusters = 0;
+  int tuned_mode = FPM_RUN_PERSISTENT;         // FPM_RUN_AUTO resolves to this
 };
 
 static void dfree(void *p) {
@@ -233,6 +238,13 @@ static int ensure_device_state(fpm_plan *p) {
   if (!d->var) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", p->m, rows);
   const size_t T = p->n_tiles, n = p->n, m = p->m;
   cudaError_t e;
+  for (const auto &v : variants())            // every fitting variant may be chosen by the autotuner
+    if (v.m == p->m && v.smem(rows) <= kMaxSmem) {
+      FPM_CK(cudaFuncSetAttribute((const void *)v.k_u16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)v.smem(rows)));
+      FPM_CK(cudaFuncSetAttribute((const void *)v.k_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)v.smem(rows)));
+    }
   if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess)
     return fail(FPM_ENOMEM, "device allocation of the tile state failed: %s", cudaGetErrorString(e));
@@ -768,13 +780,17 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   if (p->busy) return fail(FPM_EBUSY, "plan is owned by a server job");
   if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "fpm_reconstruct before fpm_load_tiles");
   if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
-  const int base = mode & 0xff;
+  int base = mode & 0xff;
   const bool graph = (mode & FPM_RUN_GRAPH) != 0;
   const bool timed = (mode & FPM_RUN_TIMED) != 0;
   const bool stall = (mode & FPM_RUN_FAULT_TEST) != 0;
   if ((mode & ~(0xff | FPM_RUN_GRAPH | FPM_RUN_TIMED | FPM_RUN_FAULT_TEST)) ||
-      (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT))
+      (base != FPM_RUN_PLAIN && base != FPM_RUN_WAVES && base != FPM_RUN_PERSISTENT && base != FPM_RUN_AUTO))
     return fail(FPM_EINVAL, "unknown mode 0x%x", mode);
+  if (base == FPM_RUN_AUTO) {
+    base = p->dev->tuned_mode;
+    mode = (mode & ~0xff) | base;
+  }
   if (timed && base != FPM_RUN_WAVES) return fail(FPM_EINVAL, "FPM_RUN_TIMED needs FPM_RUN_WAVES");
   if (stall && base != FPM_RUN_PERSISTENT) return fail(FPM_EINVAL, "FPM_RUN_FAULT_TEST needs FPM_RUN_PERSISTENT");
   cudaStream_t st = (cudaStream_t)stream;
@@ -851,6 +867,94 @@ int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t 
     jobs.push_back(fpm::QueueJob{p, iters[i]});
   }
   return fpm::run_batch(jobs, (cudaStream_t)stream, (mode & FPM_RUN_GRAPH) != 0);
+}
+
+int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entries, int32_t max_entries,
+                 int32_t *n_entries, int32_t *best) {
+  fpm::clear_error();
+  if (!p) return fail(FPM_EINVAL, "fpm_autotune: null plan");
+  if (p->busy) return fail(FPM_EBUSY, "plan is owned by a server job");
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "fpm_autotune before fpm_load_tiles");
+  if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
+  fpm::DeviceState *d = p->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rows = p->y_hi - p->y_lo + 1;
+  const size_t sb = (size_t)p->n_tiles * p->n * p->n * sizeof(float2);
+  const size_t pb = (size_t)p->n_tiles * p->m * p->m * sizeof(float2);
+  void *save = nullptr;
+  FPM_CK(cudaMalloc(&save, sb + pb));
+  struct Cand {
+    int mode;
+    const fpm::Variant *v;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  for (const auto &v : fpm::variants())
+    if (v.m == p->m && v.smem(rows) <= fpm::kMaxSmem) cands.push_back({FPM_RUN_WAVES, &v, 0.0});
+  cands.push_back({FPM_RUN_PERSISTENT, nullptr, 0.0});
+  const fpm::Variant *keep = d->var;
+  int rc = FPM_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = fail(FPM_ECUDA, "events");
+  if (rc == FPM_OK && (cudaMemcpyAsync(save, d->spec, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                       cudaMemcpyAsync((char *)save + sb, d->pup, pb, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+    rc = fail(FPM_ECUDA, "saving the state");
+  for (auto &c : cands) {
+    if (rc) break;
+    if (c.v) {
+      d->var = c.v;
+      for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);   // graphs hold the previous variant
+      d->graphs.clear();
+    }
+    for (int rep_ = 0; rep_ < 2 && rc == FPM_OK; ++rep_) {          // warm-up (graph capture), then timed
+      if (rep_ == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = fail(FPM_ECUDA, "event");
+      if (rc == FPM_OK) rc = fpm_reconstruct(p, iters, c.mode | FPM_RUN_GRAPH, stream);
+      if (rc == FPM_OK && rep_ == 1 && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(FPM_ECUDA, "event");
+      if (rc == FPM_OK && (cudaMemcpyAsync(d->spec, save, sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                           cudaMemcpyAsync(d->pup, (char *)save + sb, pb, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+        rc = fail(FPM_ECUDA, "restoring the state");
+    }
+    float ms = 0.f;
+    if (rc == FPM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = fail(FPM_ECUDA, "timing");
+    c.ms = ms;
+    if (!c.v) d->var = keep;
+  }
+  int bi = 0;
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (cands[i].ms < cands[bi].ms) bi = (int)i;
+  if (rc == FPM_OK) {
+    // the fastest wave variant serves FPM_RUN_WAVES; the fastest path serves FPM_RUN_AUTO
+    int bw = -1;
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (cands[i].v && (bw < 0 || cands[i].ms < cands[bw].ms)) bw = (int)i;
+    if (bw >= 0 && d->var != cands[bw].v) {
+      d->var = cands[bw].v;
+      for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
+      d->graphs.clear();
+    }
+    d->tuned_mode = cands[bi].mode;
+    p->cluster = d->var->c;
+    p->threads = d->var->t;
+  } else {
+    d->var = keep;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(save);
+  if (rc) return rc;
+  if (n_entries) *n_entries = (int32_t)std::min<size_t>(cands.size(), (size_t)std::max(0, max_entries));
+  if (entries)
+    for (int i = 0; i < (int)cands.size() && i < max_entries; ++i) {
+      const auto &c = cands[i];
+      entries[i].mode = c.mode;
+      entries[i].threads = c.v ? c.v->t : 384;
+      entries[i].cluster = c.v ? c.v->c : 2;
+      entries[i].ms = c.ms;
+    }
+  if (best) *best = bi;
+  return FPM_OK;
 }
 
 int fpm_get_stats(fpm_plan *p, fpm_stats *out) {

@@ -239,3 +239,25 @@ def test_persistent_wait_timeout_is_reported_and_recoverable():
     spec, _ = j.oracle_tile(0, 1)
     assert rel_l2(p.spectrum(0), spec) < SPEC_TOL
     p.close()
+
+
+def test_autotune_keeps_state_and_picks_a_bit_identical_path():
+    j = job("m128_epry")
+    p = j.plan(iters=2)
+    p.load_tiles(j.stack, j.counts_per_unit)
+    before = [p.spectrum(t) for t in range(j.w.n_tiles)]
+    entries, best = p.autotune(iters=1)
+    assert len(entries) >= 3 and all(e["ms"] > 0 for e in entries) and 0 <= best < len(entries)
+    assert {e["mode"] for e in entries} == {"waves", "persistent"}
+    for t in range(j.w.n_tiles):                        # the trials left the state as it was
+        assert np.array_equal(p.spectrum(t), before[t])
+    p.reconstruct(2, mode="auto", graph=True)
+    auto = [p.spectrum(t) for t in range(j.w.n_tiles)] + [p.pupil(t) for t in range(j.w.n_tiles)]
+    q = j.plan(iters=2)
+    q.load_tiles(j.stack, j.counts_per_unit)
+    q.reconstruct(2, mode="waves")
+    ref = [q.spectrum(t) for t in range(j.w.n_tiles)] + [q.pupil(t) for t in range(j.w.n_tiles)]
+    for a, b in zip(auto, ref):
+        assert np.array_equal(a, b)
+    p.close()
+    q.close()
