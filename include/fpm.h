@@ -120,9 +120,12 @@ typedef struct {
   int32_t max_waves;            /* largest wave count over the tiles                   */
   int32_t max_wave_width;       /* largest number of LEDs in one wave of one tile      */
   int64_t total_waves;          /* sum over tiles of their wave counts                 */
-  int64_t device_bytes;         /* device memory fpm_load_tiles will allocate          */
+  int64_t device_bytes;         /* device memory of the state fpm_load_tiles allocates
+                                   (spectra, pupils, corrections), tile images apart   */
   int32_t cluster;              /* CTAs that share one update (1 or 2)                 */
   int32_t threads;              /* threads per CTA of the update kernel                */
+  int64_t image_elems;          /* elements of the tile images fpm_load_tiles keeps
+                                   (n_tiles * n_leds * m * m, each of the stack's type) */
 } fpm_plan_info;
 
 /*
@@ -170,17 +173,20 @@ FPM_API int fpm_get_schedule(const fpm_plan *plan, int32_t *order, int32_t *shif
  *              element (l, y, x) at stack[l * stride_led + y * stride_row + x]
  *              (strides in elements; rows and LED planes must start 16-byte
  *              aligned).  Image l is the one taken with LED index l.
- *   on_device  0: `stack` is host memory; it is copied into device memory the
- *              plan owns (stream-ordered, the copy is complete when the stream
- *              reaches this point).  1: `stack` is device memory the caller
- *              keeps alive and unchanged until the plan is destroyed or loaded
- *              again; it is read in place.
+ *   on_device  0: `stack` is host memory; it is copied to a device staging
+ *              buffer that is released once the tiles are extracted.  1:
+ *              `stack` is device memory, read in place by this call's
+ *              stream-ordered work; the plan keeps no reference to it.
  *   counts_per_unit  measured intensity = element / counts_per_unit (> 0).
- * Then, per tile, the initial spectrum is the spectrum of the upsampled centre
- * image: (N/m)^2 * zero-pad_N(centred DFT_m(sqrt(I_first))), I_first being the
- * tile's image of the first LED of the order, and the pupil is reset to the
- * initial pupil.  Allocates the plan's device state on first use
- * (FPM_ENOMEM on failure).
+ * Every tile's m x m window of every image is copied into device memory the
+ * plan owns (image_elems elements of the stack's type, see fpm_plan_info),
+ * column by column, in the order the update kernel's column transform reads
+ * it.  Then, per tile, the initial spectrum is the spectrum of the upsampled
+ * centre image: (N/m)^2 * zero-pad_N(centred DFT_m(sqrt(I_first))), I_first
+ * being the tile's image of the first LED of the order, and the pupil is reset
+ * to the initial pupil.  Allocates the plan's device state on first use
+ * (FPM_ENOMEM on failure); loading images of another type reallocates the
+ * tile images.
  */
 FPM_API int fpm_load_tiles(fpm_plan *plan, const void *stack, int32_t dtype, int32_t on_device,
                    int64_t stride_led, int64_t stride_row, float counts_per_unit,
@@ -342,7 +348,8 @@ FPM_API int fpm_server_destroy(fpm_server *server);
  *   m in {64, 128, 192, 256}; n = 2..8 times m.
  * It computes exactly what fpm_reconstruct computes for a wave holding this one
  * LED: the max |P|^2 normaliser of the current pupil, the spectrum update and,
- * with epry, the pupil correction added.  Every temporary lives in a fixed
+ * with epry, the pupil correction added.  Every temporary (the correction,
+ * the tables and the image rearranged for the kernel) lives in a fixed
  * 1 MiB array of static device memory that each device loading the library
  * holds until the process exits; sizes needing more are rejected with
  * FPM_EINVAL.  All calls on a device share that array, so calls that overlap

@@ -54,6 +54,7 @@ class PlanInfo(C.Structure):
         ("iters", C.c_int32), ("support_px", C.c_int32), ("support_rows", C.c_int32),
         ("max_waves", C.c_int32), ("max_wave_width", C.c_int32), ("total_waves", C.c_int64),
         ("device_bytes", C.c_int64), ("cluster", C.c_int32), ("threads", C.c_int32),
+        ("image_elems", C.c_int64),
     ]
 
     def as_dict(self):

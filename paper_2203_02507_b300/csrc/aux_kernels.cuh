@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "dft.cuh"
+#include "tile_images.cuh"
 #include "update_args.h"
 
 namespace fpm {

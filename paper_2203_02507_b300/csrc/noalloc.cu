@@ -7,7 +7,8 @@
 // camera.  fpm_update_tile_static serves them: the caller passes the spectrum,
 // the pupil and the measured image, and every temporary the update needs (the
 // pupil correction, the support chords, the twiddle tables, the one-item work
-// list and the merge entry) lives in the file-scope array below.
+// list, the merge entry and the image rearranged into the update kernel's
+// column layout) lives in the file-scope array below.
 //
 // The array is a fixed 1 MiB per device that loads this library, held until
 // the process exits.  All calls on a device share it and it keeps the last
@@ -22,6 +23,7 @@
 
 #include "internal.h"
 #include "runtime.h"
+#include "tile_images.cuh"
 
 namespace fpm {
 
@@ -74,12 +76,13 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   if (m < 16 || m > 4096 || m % 16) return fail(FPM_EINVAL, "tile side %d out of range", m);
   if (n < 2 * m || n > 8 * m || n % m)
     return fail(FPM_EINVAL, "HR side %d must be 2..8 times the tile side %d", n, m);
-  // layout of the static array: [pupil correction m*m][tables]
+  // layout of the static array: [pupil correction m*m][tables][image in the kernel's column layout]
   const size_t dp_bytes = (size_t)m * m * sizeof(float2);
   const size_t blob_off = fpm::align256(dp_bytes);
   const size_t chords_b = (size_t)m * sizeof(int2), tw_b = (size_t)m * sizeof(float2);
   const size_t blob_bytes = chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + sizeof(int2);
-  const size_t need = blob_off + blob_bytes;
+  const size_t img_off = fpm::align256(blob_off + blob_bytes);
+  const size_t need = img_off + (size_t)m * m * sizeof(float);
   if (need > fpm::kStaticScratchBytes)
     return fail(FPM_EINVAL, "tile side %d needs %zu bytes of static scratch; the limit is %zu", m, need,
                 fpm::kStaticScratchBytes);
@@ -136,7 +139,14 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   const int2 *d_sh = reinterpret_cast<const int2 *>(d_item + 1);
   const int2 *d_mg = d_sh + 2;
   float2 *d_dp = reinterpret_cast<float2 *>(dev);
+  float *d_img = reinterpret_cast<float *>(dev + img_off);
   float2 *pup = static_cast<float2 *>(pupil);
+
+  // 0. the image in the update kernel's column layout
+  fpm::tile_images_kernel<float><<<m / 32, 256, (size_t)m * 33 * sizeof(unsigned), st>>>(
+      d_img, image, (long long)m * m, m, d_sh + 1, m, fa, fb, 1, m / 32);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "image layout: %s", cudaGetErrorString(e));
 
   // 1. zero the correction (the merge sums whole pixel pairs, so entries off this
   //    call's support must be zero)  2. the update  3. (EPRY) add the correction
@@ -150,13 +160,10 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   a.dpup = epry ? d_dp : nullptr;
   a.items = d_item;
   a.shifts = d_sh;
-  a.origins = d_sh + 1;
   a.chords = d_chords;
   a.tw_inv = d_twi;
   a.tw_fwd = d_twf;
-  a.stack = image;
-  a.stride_led = (long long)m * m;
-  a.stride_row = m;
+  a.images = d_img;
   a.inv_counts = 1.f;
   a.scale = (float)((double)n / m * (double)n / m);
   a.n = n;

@@ -404,6 +404,7 @@ int fpm_plan_get_info(const fpm_plan *p, fpm_plan_info *info) {
   info->device_bytes = T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + p->max_width : 1);
   info->cluster = p->cluster;
   info->threads = p->threads;
+  info->image_elems = T * p->n_leds * m * m;
   return FPM_OK;
 }
 

@@ -52,10 +52,12 @@ using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256, 1>;
 using Cfg192c = UpdateCfg<192, 12, 16, 16, 2, 256, 1>;
 using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
+using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),
                                          make_variant<Cfg128w>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),
+                                         make_variant<Cfg256x>(),
                                          make_variant<Cfg256w>(), make_variant<Cfg256>()};
   return v;
 }
@@ -169,11 +171,9 @@ struct DeviceState {
   float2 *twl_fwd_m = nullptr;                      // line FFT tables
 
   unsigned *err = nullptr;
-  void *stack_owned = nullptr;
-  size_t stack_owned_bytes = 0;
-  const void *stack = nullptr;
+  void *images = nullptr;                          // [T][L][m][m] column layout (tile_image_offset)
+  size_t images_bytes = 0;
   int32_t dtype = FPM_U16;
-  long long stride_led = 0, stride_row = 0;
   float inv_counts = 1.f;
   bool loaded = false;
   const Variant *var = nullptr;
@@ -214,7 +214,7 @@ void destroy_device_state(fpm_plan *p) {
   }
   for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
                   (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
-                  d->stack_owned})
+                  d->images})
     dfree(q);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -311,7 +311,7 @@ static unsigned grid_for(long long n, int threads) {
 }
 
 // Initial guess of every tile from its image of the first LED in the order.
-static int run_init(fpm_plan *p, cudaStream_t st) {
+static int run_init(fpm_plan *p, const void *stack, long long stride_led, long long stride_row, cudaStream_t st) {
   DeviceState *d = p->dev;
   const int m = p->m, n = p->n, T = p->n_tiles;
   float2 *tmp = nullptr;
@@ -320,11 +320,10 @@ static int run_init(fpm_plan *p, cudaStream_t st) {
   const int led = p->order[0];
   if (d->dtype == FPM_U16)
     init_gather_kernel<uint16_t><<<grid_for(tot, 256), 256, 0, st>>>(
-        tmp, (const uint16_t *)d->stack, d->stride_led, d->stride_row, d->origins, led, m, T, d->inv_counts);
+        tmp, (const uint16_t *)stack, stride_led, stride_row, d->origins, led, m, T, d->inv_counts);
   else
-    init_gather_kernel<float><<<grid_for(tot, 256), 256, 0, st>>>(tmp, (const float *)d->stack, d->stride_led,
-                                                                    d->stride_row, d->origins, led, m, T,
-                                                                    d->inv_counts);
+    init_gather_kernel<float><<<grid_for(tot, 256), 256, 0, st>>>(tmp, (const float *)stack, stride_led, stride_row,
+                                                                    d->origins, led, m, T, d->inv_counts);
   int rc;
   // rows then columns of every tile
   if ((rc = launch_fft_lines(tmp, d->twl_fwd_m, m, -1, (long long)T * m, m, (long long)m * m, m, 1, st))) return rc;
@@ -336,7 +335,7 @@ static int run_init(fpm_plan *p, cudaStream_t st) {
   FPM_CK(cudaFreeAsync(tmp, st));
   // pupils into buffer 0
   FPM_CK(cudaMemcpyAsync(d->pup, p->pupil0.data(), (size_t)T * m * m * sizeof(float2), cudaMemcpyHostToDevice, st));
-  d->load_launches = 4;   // gather, 2 x line FFT, place
+  d->load_launches = 5;   // tile images, gather, 2 x line FFT, place
   return FPM_OK;
 }
 
@@ -362,13 +361,10 @@ static UpdateArgs make_args(fpm_plan *p, const StepDev *sd) {
   a.dpup = p->epry ? d->dpup : nullptr;
   a.items = sd ? sd->items : nullptr;
   a.shifts = d->shifts;
-  a.origins = d->origins;
   a.chords = d->chords;
   a.tw_inv = d->tw_inv;
   a.tw_fwd = d->tw_fwd;
-  a.stack = d->stack;
-  a.stride_led = d->stride_led;
-  a.stride_row = d->stride_row;
+  a.images = d->images;
   a.inv_counts = d->inv_counts;
   a.scale = (float)((double)p->n / p->m * (double)p->n / p->m);
   a.n = p->n;
@@ -735,6 +731,28 @@ int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device,
   if (rc) return rc;
   if ((rc = ensure_device_state(p))) return rc;
   DeviceState *d = p->dev;
+  const size_t ib = image_bytes(p, dtype);
+  if (d->images_bytes != ib) {
+    // queues and graphs hold the image address: drop them with the old buffer
+    cudaDeviceSynchronize();
+    for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
+    d->graphs.clear();
+    d->graph_launches.clear();
+    for (auto &kv : d->queues) free_queue(kv.second);
+    d->queues.clear();
+    forget_batches(p);
+    if (d->images) cudaFree(d->images);
+    d->images = nullptr;
+    d->images_bytes = 0;
+    d->loaded = false;
+    if (cudaMalloc(&d->images, ib) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FPM_ENOMEM, "device allocation of the tile images (%zu bytes) failed", ib);
+    }
+    d->images_bytes = ib;
+  }
+  const void *src = stack;
+  void *staging = nullptr;        // a host stack passes through device memory once, for the gather
   if (on_device) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, stack) != cudaSuccess ||
@@ -742,32 +760,44 @@ int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device,
       cudaGetLastError();
       return fail(FPM_EINVAL, "on_device stack is not device memory");
     }
-    d->stack = stack;
   } else {
-    if (d->stack_owned_bytes < bytes) {
-      if (d->stack_owned) cudaFree(d->stack_owned);
-      d->stack_owned = nullptr;
-      d->stack_owned_bytes = 0;
-      cudaError_t e = cudaMalloc(&d->stack_owned, bytes);
-      if (e != cudaSuccess) return fail(FPM_ENOMEM, "device allocation of the image stack (%zu bytes) failed", bytes);
-      d->stack_owned_bytes = bytes;
+    if (cudaMallocAsync(&staging, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FPM_ENOMEM, "device staging of the image stack (%zu bytes) failed", bytes);
     }
-    FPM_CK(cudaMemcpyAsync(d->stack_owned, stack, bytes, cudaMemcpyHostToDevice, st));
-    d->stack = d->stack_owned;
+    FPM_CK(cudaMemcpyAsync(staging, stack, bytes, cudaMemcpyHostToDevice, st));
+    src = staging;
   }
   d->dtype = dtype;
-  d->stride_led = stride_led;
-  d->stride_row = stride_row;
   d->inv_counts = 1.0f / counts_per_unit;
   FPM_CK(cudaMemsetAsync(d->err, 0, 4 * sizeof(unsigned), st));   // a reload clears a previous failure
-  if ((rc = run_init(p, st))) return rc;
+  // every tile's images in the update kernel's column layout
+  const int m = p->m;
+  const long long n_blocks = (long long)p->n_tiles * p->n_leds * (m / 32);
+  const unsigned grid = (unsigned)std::min<long long>(n_blocks, 148LL * 16);
+  const size_t smem = (size_t)m * 33 * sizeof(unsigned);
+  if (dtype == FPM_U16)
+    tile_images_kernel<uint16_t><<<grid, 256, smem, st>>>((uint16_t *)d->images, (const uint16_t *)src, stride_led,
+                                                          stride_row, d->origins, m, d->var->a, d->var->b, p->n_leds,
+                                                          n_blocks);
+  else
+    tile_images_kernel<float><<<grid, 256, smem, st>>>((float *)d->images, (const float *)src, stride_led, stride_row,
+                                                       d->origins, m, d->var->a, d->var->b, p->n_leds, n_blocks);
+  FPM_CK(cudaGetLastError());
+  rc = run_init(p, src, stride_led, stride_row, st);
+  if (staging) cudaFreeAsync(staging, st);
+  if (rc) return rc;
   d->loaded = true;
   return FPM_OK;
 }
 
-size_t plan_device_bytes(const fpm_plan *p) {
+size_t image_bytes(const fpm_plan *p, int32_t dtype) {
+  return (size_t)p->n_tiles * p->n_leds * p->m * p->m * (dtype == FPM_U16 ? 2 : 4);
+}
+
+size_t plan_device_bytes(const fpm_plan *p, int32_t dtype) {
   const size_t T = p->n_tiles, n = p->n, m = p->m;
-  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1);
+  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1) + image_bytes(p, dtype);
 }
 
 }  // namespace fpm

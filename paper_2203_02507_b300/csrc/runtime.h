@@ -30,8 +30,11 @@ int validate_stack(fpm_plan *p, const void *stack, int32_t dtype, int64_t stride
 // fpm_load_tiles without the ownership check (the server loads the plans it owns).
 int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
                int64_t stride_row, float counts_per_unit, cudaStream_t st);
-// Device bytes a plan's state takes once loaded (spectra, pupils, corrections).
-size_t plan_device_bytes(const fpm_plan *p);
+// Device bytes of a plan's tile images (the update kernel's column layout) of type dtype.
+size_t image_bytes(const fpm_plan *p, int32_t dtype);
+// Device bytes a plan takes once loaded with images of type dtype (spectra,
+// pupils, corrections and the tile images).
+size_t plan_device_bytes(const fpm_plan *p, int32_t dtype);
 // Device-side description of a loaded plan for the update kernel (items unset).
 UpdateArgs plan_update_args(fpm_plan *p);
 // Image element type of a loaded plan (FPM_U16 / FPM_F32); -1 if not loaded.

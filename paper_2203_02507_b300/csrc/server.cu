@@ -196,14 +196,17 @@ int fpm_submit(fpm_server *s, fpm_plan *p, int32_t iters, const void *stack, int
   fpm::clear_error();
   if (!s || !p || !out) return fail(FPM_EINVAL, "fpm_submit: null argument");
   if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
-  size_t bytes = fpm::plan_device_bytes(p);
+  size_t bytes = 0;
   if (stack) {
     size_t sb = 0;
     int rc = fpm::validate_stack(p, stack, dtype, stride_led, stride_row, counts_per_unit, &sb);
     if (rc) return rc;
-    if (!on_device) bytes += sb;
+    bytes = fpm::plan_device_bytes(p, dtype);
+    if (!on_device) bytes += sb;      // the stack's device staging while it loads
   } else if (fpm::plan_image_dtype(p) < 0) {
     return fail(FPM_ESTATE, "plan has no images: pass a stack or call fpm_load_tiles first");
+  } else {
+    bytes = fpm::plan_device_bytes(p, fpm::plan_image_dtype(p));
   }
   if (bytes > s->budget)
     return fail(FPM_EBUDGET, "job needs %zu device bytes, more than the server's budget %zu", bytes, s->budget);

@@ -47,14 +47,35 @@ namespace fpm {
 __device__ __forceinline__ int inter_swz(int y, int p) { return p ^ ((y ^ (p >> 4)) & 15); }
 __device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz(y, p); }
 
-template <typename Img>
-__device__ __forceinline__ float load_image(const Img *img, long long off) {
-  if constexpr (sizeof(Img) == 2) {
-    return (float)__ldg(reinterpret_cast<const unsigned short *>(img) + off);
-  } else {
-    return __ldg(reinterpret_cast<const float *>(img) + off);
+// B consecutive image elements of one column (one lane's pixels in the column
+// phase), fetched with 16-byte loads and kept packed until they are used.
+template <typename Img, int B>
+struct ImgCol {
+  static_assert(B % 8 == 0, "a lane's pixels span whole 16-byte words");
+  static constexpr int WORDS = (int)(B * sizeof(Img) / 4);
+  unsigned w[WORDS];
+  __device__ __forceinline__ void load(const Img *p) {
+#pragma unroll
+    for (int i = 0; i < WORDS / 4; ++i) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+      w[4 * i] = v.x;
+      w[4 * i + 1] = v.y;
+      w[4 * i + 2] = v.z;
+      w[4 * i + 3] = v.w;
+    }
   }
-}
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < WORDS; ++i) w[i] = 0u;
+  }
+  __device__ __forceinline__ float get(int k) const {
+    if constexpr (sizeof(Img) == 2) {
+      return (float)((w[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+    } else {
+      return __uint_as_float(w[k]);
+    }
+  }
+};
 
 template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1>
 struct UpdateCfg {
@@ -65,6 +86,7 @@ struct UpdateCfg {
   static constexpr int UA = (B + TPT - 1) / TPT;   // units of the radix-A passes per lane
   static constexpr int UB = (A + TPT - 1) / TPT;   // units of the radix-B passes per lane
   static_assert(A * B == M, "m = A * B");
+  static_assert(A == image_split_a(M), "the tile images are laid out for the canonical split of m");
   static_assert(32 % TPT == 0 && T % 32 == 0, "groups must not straddle warps");
   static_assert(W % 16 == 0, "inter rows are swizzled in groups of 16");
   static_assert(T <= 512, "the normaliser holds one partial per warp in 16 slots");
@@ -111,9 +133,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const size_t mm = (size_t)M * M;
   const float2 *__restrict__ pup = a.pup + (size_t)tile * mm;
   float2 *dp_out = a.dpup ? a.dpup + ((size_t)tile * a.slots + slot) * mm : nullptr;
-  const int2 org = a.origins[tile];
-  const Img *img = reinterpret_cast<const Img *>(a.stack) + (long long)led * a.stride_led +
-                   (long long)org.x * a.stride_row + org.y;
+  // this CTA's first column of the tile image (column-permuted layout)
+  const Img *img = reinterpret_cast<const Img *>(a.images) + tile_image_offset(tile, led, a.n_leds, M) +
+                   (size_t)q * W * M;
 
   for (int i = tid; i < M; i += T) {
     twi[i] = a.tw_inv[i];
@@ -214,21 +236,19 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       if (b < B && y >= y_lo && y <= y_hi) out_mask[u] |= 1u << k2;
     }
   }
-  // measured pixels of this lane's rows y = k1 + A k2, one column ahead
-  float meas[Cfg::UB][B];
-  auto fetch = [&](int col, float (&dst)[Cfg::UB][B]) {
+  // measured pixels of this lane's rows y = k1 + A k2 (B contiguous elements), one column ahead
+  ImgCol<Img, B> meas[Cfg::UB];
+  auto fetch = [&](int col, ImgCol<Img, B> (&dst)[Cfg::UB]) {
 #pragma unroll
     for (int u = 0; u < Cfg::UB; ++u) {
       const int k1 = tl + u * TPT;
-#pragma unroll
-      for (int k2 = 0; k2 < B; ++k2)
-        dst[u][k2] = (k1 < A && col < W) ? load_image<Img>(img, (long long)(k1 + A * k2) * a.stride_row + q * W + col)
-                                         : 0.f;
+      if (k1 < A && col < W) dst[u].load(img + (size_t)col * M + k1 * B);
+      else dst[u].zero();
     }
   };
   fetch(g, meas);
   for (int c = g; c < W; c += G) {
-    float next[Cfg::UB][B];
+    ImgCol<Img, B> next[Cfg::UB];
     fetch(c + G, next);
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
@@ -254,23 +274,28 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
         for (int bb = 0; bb < B; ++bb) v[bb] = scr[bb * (A + 1) + k1];
         Dft<B, 1>::run(v);
-        // amplitude step at y = k1 + A k2
+        // amplitude step at y = k1 + A k2, without branches: sqrt(I) / |phi~| =
+        // I / sqrt(I |phi~|^2), the hardware reciprocal square root refined by one
+        // Newton-Raphson step, r += r (1 - x r^2) / 2.  Pixels with phi~ = 0 (rare)
+        // are flagged and take sqrt(I) afterwards.
+        unsigned zmask = 0;
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const float in = fmaxf(__fmul_rn(meas[u][k2], a.inv_counts), 0.f);
+          const float in = fmaxf(__fmul_rn(meas[u].get(k2), a.inv_counts), 0.f);
           const float2 f = v[k2];
           const float m2 = cabs2(f);
-          if (m2 > 0.f) {
-            // sqrt(I) / |phi~| = I / sqrt(I |phi~|^2); the hardware reciprocal square root
-            // is refined by one Newton-Raphson step, r += r (1 - x r^2) / 2
-            const float x = __fmul_rn(in, m2);
-            float r = rsqrtf(x);
-            r = __fmaf_rn(__fmul_rn(0.5f, r), __fmaf_rn(-__fmul_rn(x, r), r, 1.0f), r);
-            const float s = (in > 0.f) ? __fmul_rn(in, r) : 0.f;
-            v[k2] = cscale(f, s);
-          } else {
-            v[k2] = make_float2(sqrtf(in), 0.f);
-          }
+          const float x = __fmul_rn(in, m2);
+          float r = rsqrtf(x);
+          r = __fmaf_rn(__fmul_rn(0.5f, r), __fmaf_rn(-__fmul_rn(x, r), r, 1.0f), r);
+          const float s = (in > 0.f) ? __fmul_rn(in, r) : 0.f;
+          const float2 scaled = cscale(f, s);
+          v[k2] = (m2 > 0.f) ? scaled : make_float2(0.f, 0.f);
+          zmask |= (m2 > 0.f) ? 0u : (1u << k2);
+        }
+        if (zmask) {
+#pragma unroll
+          for (int k2 = 0; k2 < B; ++k2)
+            if ((zmask >> k2) & 1u) v[k2] = make_float2(sqrtf(fmaxf(__fmul_rn(meas[u].get(k2), a.inv_counts), 0.f)), 0.f);
         }
         // forward DFT, first pass of the B x A split: unit b' = k1, over a' = k2
         Dft<B, -1>::run(v);
@@ -303,9 +328,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
     }
     __syncwarp(gmask);
 #pragma unroll
-    for (int u = 0; u < Cfg::UB; ++u)
-#pragma unroll
-      for (int k2 = 0; k2 < B; ++k2) meas[u][k2] = next[u][k2];
+    for (int u = 0; u < Cfg::UB; ++u) meas[u] = next[u];
   }
   if constexpr (C > 1) {
     cg::this_cluster().sync();

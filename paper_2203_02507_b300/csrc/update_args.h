@@ -8,18 +8,27 @@ namespace fpm {
 // Row chunks of the pupil merge (merge_kernel).
 constexpr int kNormParts = 8;
 
+// Image layout read by the update kernel (m = A * B, the kernel's split): for
+// tile t and LED l the m x m image is stored column after column, and within
+// column x position k1 * B + k2 holds row y = k1 + A * k2, the order in which
+// the radix-B pass of the column transform consumes it.  One lane's B pixels
+// are then contiguous.
+// The split of each supported tile side; every kernel for that side uses it.
+constexpr int image_split_a(int m) { return m == 64 ? 8 : m == 128 ? 16 : m == 192 ? 12 : m == 256 ? 16 : 0; }
+__host__ __device__ inline size_t tile_image_offset(int t, int l, int n_leds, int m) {
+  return ((size_t)t * n_leds + l) * (size_t)m * m;
+}
+
 struct UpdateArgs {
   float2 *spec;               // [T][N][N] centred spectra
   const float2 *pup;          // [T][m][m] centred pupils (as of the update's wave start)
   float2 *dpup;               // [T][slots][m][m] pupil corrections (EPRY) or null; zero off the support
   const int4 *items;          // (tile, led, slot, sequence index)
   const int2 *shifts;         // [T][L] (sy, sx)
-  const int2 *origins;        // [T] (y0, x0) on the sensor
   const int2 *chords;         // [m] (lo, hi) support columns per box row
   const float2 *tw_inv;       // [m] exp(+2 pi i b k1/m) at k1*B + b
   const float2 *tw_fwd;       // [m] exp(-2 pi i b k1/m) at k1*A + b (the B x A split)
-  const void *stack;          // images, element (l, y, x) at l*stride_led + y*stride_row + x
-  long long stride_led, stride_row;
+  const void *images;         // [T][L][m][m] tile images in the column layout below
   float inv_counts;           // intensity = element * inv_counts
   float scale;                // (N/m)^2
   int n;                      // N

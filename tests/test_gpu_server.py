@@ -96,7 +96,8 @@ def test_admission_by_budget_and_overlap():
     w_small, w_big = MIX[0], MIX[3]
     js, jb = job(w_small), job(w_big)
     pb = jb.plan()
-    need_big = pb.info["device_bytes"] + jb.stack.nbytes
+    # state + tile images (uint16) + the host stack's device staging while it loads
+    need_big = pb.info["device_bytes"] + 2 * pb.info["image_elems"] + jb.stack.nbytes
     # a budget that holds the big job but not two of them
     srv = Server(int(need_big * 1.5))
     pb2 = jb.plan()
