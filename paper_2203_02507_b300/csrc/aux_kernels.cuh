@@ -103,16 +103,19 @@ static __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, i
 
 // Close a wave of a tile: add its ns pupil corrections to the pupil in slot
 // (= sequence) order.  Corrections are zero off the support (the update writes
-// them only there and they start zeroed) and so is the pupil, so whole aligned
-// pixel pairs of each support row's chord are summed with 16-byte loads, all
-// of a pair's corrections in flight together.  Rows are cut into `parts`
-// chunks; merge_rows does chunk `part` with the threads [t0, t0 + nt) of the
-// calling CTA(s).
+// them only there and they start zeroed) and so is the pupil, so any pixel set
+// that covers the support gives the same sums: each warp takes whole rows and
+// its lanes the aligned pixel pairs within the row's disc bound (disc = 1; else
+// the whole row), summed with 16-byte loads, two pairs and up to kMergeSlots
+// corrections of each in flight together, no table read first.  Rows are cut
+// into `parts` chunks; merge_rows does chunk `part` with the threads
+// [t0, t0 + nt) of the calling CTA(s) (t0 and nt multiples of 32).
 constexpr int kMergeSlots = 8;   // corrections loaded together
+constexpr int kMergePairs = 2;   // pixel pairs per lane in flight
 
-__device__ __forceinline__ void merge_rows(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
-                                           const int2 *__restrict__ chords, int t, int ns, int part, int parts,
-                                           int y_lo, int rows, int m, int slots, int t0, int nt) {
+__device__ __forceinline__ void merge_rows(float2 *__restrict__ pup, const float2 *__restrict__ dpup, int t, int ns,
+                                           int part, int parts, int y_lo, int rows, int m, int slots, int disc,
+                                           int t0, int nt) {
   if (ns <= 0) return;
   const int rpp = (rows + parts - 1) / parts;
   const int r0 = part * rpp, r1 = min(rows, r0 + rpp);
@@ -120,32 +123,49 @@ __device__ __forceinline__ void merge_rows(float2 *__restrict__ pup, const float
   const size_t mm2 = (size_t)m * m / 2;                   // float4 per pupil
   float4 *p = reinterpret_cast<float4 *>(pup + (size_t)t * m * m);
   const float4 *d = reinterpret_cast<const float4 *>(dpup + (size_t)t * slots * m * m);
-  for (int idx = t0; idx < (r1 - r0) * hp; idx += nt) {
-    const int by = y_lo + r0 + idx / hp, pr = idx % hp;
-    const int2 ch = chords[by];
-    if (2 * pr + 1 < ch.x || 2 * pr > ch.y) continue;
-    const size_t off = (size_t)by * hp + pr;
-    float4 v = p[off];
-    for (int s0 = 0; s0 < ns; s0 += kMergeSlots) {
-      float4 a[kMergeSlots];
+  const int lane = t0 & 31, warp = t0 >> 5, warps = nt >> 5;
+  for (int r = r0 + warp; r < r1; r += warps) {
+    const int by = y_lo + r;
+    const int hw = disc ? disc_half_width(by, y_lo, rows) : m;
+    const int plo = max(0, m / 2 - hw) >> 1, phi = min(m - 1, m / 2 + hw) >> 1;   // pairs touching the bound
+    for (int pr0 = plo + lane; pr0 <= phi; pr0 += 32 * kMergePairs) {
+      size_t off[kMergePairs];
+      bool act[kMergePairs];
+      float4 v[kMergePairs];
 #pragma unroll
-      for (int k = 0; k < kMergeSlots; ++k)
-        a[k] = (s0 + k < ns) ? d[(size_t)(s0 + k) * mm2 + off] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < kMergePairs; ++u) {
+        const int pr = pr0 + 32 * u;
+        act[u] = pr <= phi;
+        off[u] = (size_t)by * hp + pr;
+        v[u] = act[u] ? p[off[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int s0 = 0; s0 < ns; s0 += kMergeSlots) {
+        float4 a[kMergePairs][kMergeSlots];
 #pragma unroll
-      for (int k = 0; k < kMergeSlots; ++k)
-        if (s0 + k < ns) v = make_float4(v.x + a[k].x, v.y + a[k].y, v.z + a[k].z, v.w + a[k].w);
+        for (int u = 0; u < kMergePairs; ++u)
+#pragma unroll
+          for (int k = 0; k < kMergeSlots; ++k)
+            a[u][k] = (act[u] && s0 + k < ns) ? d[(size_t)(s0 + k) * mm2 + off[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kMergePairs; ++u)
+#pragma unroll
+          for (int k = 0; k < kMergeSlots; ++k)
+            if (s0 + k < ns)
+              v[u] = make_float4(v[u].x + a[u][k].x, v[u].y + a[u][k].y, v[u].z + a[u][k].z, v[u].w + a[u][k].w);
+      }
+#pragma unroll
+      for (int u = 0; u < kMergePairs; ++u)
+        if (act[u]) p[off[u]] = v[u];
     }
-    p[off] = v;
   }
 }
 
 // Grid: (entries (tile, slots), kNormParts row chunks).
 static __global__ void __launch_bounds__(256) merge_kernel(float2 *__restrict__ pup, const float2 *__restrict__ dpup,
-                                                           const int2 *__restrict__ entries,
-                                                           const int2 *__restrict__ chords, int y_lo, int rows, int m,
-                                                           int slots) {
+                                                           const int2 *__restrict__ entries, int y_lo, int rows, int m,
+                                                           int slots, int disc) {
   const int2 e = entries[blockIdx.x];
-  merge_rows(pup, dpup, chords, e.x, e.y, blockIdx.y, kNormParts, y_lo, rows, m, slots, threadIdx.x, blockDim.x);
+  merge_rows(pup, dpup, e.x, e.y, blockIdx.y, kNormParts, y_lo, rows, m, slots, disc, threadIdx.x, blockDim.x);
 }
 
 // Simulator: box of the unshifted DFT spectrum times the pupil, placed in

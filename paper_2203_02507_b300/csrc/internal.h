@@ -49,6 +49,7 @@ struct fpm_plan {
   std::vector<uint8_t> support;     // [m][m]
   std::vector<int32_t> chord_lo, chord_hi;   // [m], per box row; lo > hi when empty
   int32_t y_lo = 0, y_hi = -1;      // support rows (box coordinates)
+  bool disc_ok = false;             // disc_half_width bounds every chord
   int32_t support_px = 0;
   int32_t max_waves = 0, max_width = 0;
   int64_t total_waves = 0;
@@ -72,6 +73,9 @@ namespace fpm {
 // lo/hi (and mask, if not null) must hold m (m * m) entries.
 int support_chords(int m, double df, double na, double wavelength_um, uint8_t *mask, int32_t *lo, int32_t *hi,
                    int32_t *y_lo, int32_t *y_hi);
+// True if disc_half_width (the kernels' table-free chord bound) covers every
+// support chord [lo[by], hi[by]], by in [y_lo, y_hi].
+bool disc_bound_covers(int m, int32_t y_lo, int32_t y_hi, const int32_t *lo, const int32_t *hi);
 // Build (or fetch from the cache) the wave-step lists for the first `iters` loops.
 const StepLists &step_lists(fpm_plan *p, int32_t iters);
 // Free device state (runtime.cu).

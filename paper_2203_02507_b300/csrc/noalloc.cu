@@ -171,8 +171,10 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   a.y_lo = y_lo;
   a.rows = rows;
   a.slots = 1;
+  a.disc = fpm::disc_bound_covers(m, y_lo, y_hi, lo, hi) ? 1 : 0;
   a.err = nullptr;
   if ((rc = fpm::launch_update_items(m, rows, FPM_F32, a, 0, 1, st))) return rc;
-  if (epry && (rc = fpm::launch_merge(pup, d_dp, d_mg, 1, d_chords, y_lo, rows, m, 1, st))) return rc;
+  const int disc = a.disc;
+  if (epry && (rc = fpm::launch_merge(pup, d_dp, d_mg, 1, y_lo, rows, m, 1, disc, st))) return rc;
   return FPM_OK;
 }

@@ -57,19 +57,25 @@ struct PersistArgs {
   long long timeout_ns;
 };
 
-// One launch shape for every tile side: 2-CTA clusters of 384 threads.
-constexpr int kPC = 2, kPT = 384;
+// 2-CTA clusters of 384 threads for every tile side; a queue whose jobs all
+// have tiles of 256 runs 448 threads (14 warps, 144 registers each: the
+// column phase's 128 columns per CTA then take 5 rounds of 28 transforms).
+constexpr int kPC = 2, kPT = 384, kPT256 = 448;
 using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1>;
 using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1>;
 using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1>;
 using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1>;
+using P256x = UpdateCfg<256, 16, 16, 16, kPC, kPT256, 1, 0>;
 
-static size_t persistent_smem(int m, int rows) {
+template <int MSEL>
+constexpr int persistent_threads() { return MSEL == 256 ? kPT256 : kPT; }
+
+static size_t persistent_smem(int m, int rows, int msel) {
   switch (m) {
     case 64: return P64::smem_bytes(rows);
     case 128: return P128::smem_bytes(rows);
     case 192: return P192::smem_bytes(rows);
-    default: return P256::smem_bytes(rows);
+    default: return msel == 256 ? P256x::smem_bytes(rows) : P256::smem_bytes(rows);
   }
 }
 
@@ -108,69 +114,95 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
 // MSEL = 0: any tile side (dispatch per entry); MSEL = m: every job has tile side m,
 // so the kernel carries only that variant (and its register needs).
 template <typename Img, int MSEL>
-__global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constant__ PersistArgs pa) {
+__global__ void __launch_bounds__(persistent_threads<MSEL>(), 1) persistent_kernel(const __grid_constant__ PersistArgs pa) {
   extern __shared__ float4 smem_raw[];
-  __shared__ int s_idx, s_flag;
+  // the cluster leader claims the next entry while the current one waits on its
+  // dependency and hands both to the cluster through these (entries double-
+  // buffered).  s_ok (dependency met) and s_last (wave completed) are separate:
+  // between a read of either and the leader's next write of it lies a cluster
+  // barrier inside the update.
+  __shared__ int s_idx[2], s_ok, s_last;
+  __shared__ PItem s_item[2];
   cg::cluster_group cl = cg::this_cluster();
   const unsigned q = cl.block_rank();
   const bool leader = q == 0 && threadIdx.x == 0;
-  for (;;) {
-    if (leader) {
-      int idx = (int)atomicAdd(pa.next, 1u);
-      if (load_acquire(&pa.err[1])) idx = pa.n_items;
-      for (int r = 0; r < kPC; ++r) *cl.map_shared_rank(&s_idx, r) = idx;
+  // one tile side: its twiddles stay in shared memory for the whole run (the
+  // first cluster barrier below orders them before any update reads them)
+  if constexpr (MSEL == 64) load_twiddles<P64>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
+  if constexpr (MSEL == 128) load_twiddles<P128>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
+  if constexpr (MSEL == 192) load_twiddles<P192>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
+  if constexpr (MSEL == 256) load_twiddles<P256x>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
+  constexpr bool load_tw = MSEL == 0;   // mixed tile sides reload them per update
+  if (leader) {
+    const int idx = (int)atomicAdd(pa.next, 1u);
+    const PItem it = idx < pa.n_items ? pa.items[idx] : PItem{};
+    for (int r = 0; r < kPC; ++r) {
+      *cl.map_shared_rank(&s_idx[0], r) = idx;
+      *cl.map_shared_rank(&s_item[0], r) = it;
     }
-    cl.sync();
-    const int idx = s_idx;
-    if (idx >= pa.n_items) break;
-    const PItem it = pa.items[idx];
+  }
+  cl.sync();
+  for (int k = 0;; k ^= 1) {
+    if (s_idx[k] >= pa.n_items) break;
     if (leader) {
+      const PItem it = s_item[k];
+      int nidx = (int)atomicAdd(pa.next, 1u);        // claim ahead; its latency overlaps the wait
       const unsigned want = pa.stall_test ? 0xffffffffu : (unsigned)it.wave;
       const bool ok = wait_for(&pa.merged[it.tile], want, &pa.err[1], pa.timeout_ns);
       if (!ok) {
         atomicOr(&pa.err[0], 1u);        // a dependency wait ran out (or another did)
         atomicExch(&pa.err[1], 1u);
       }
-      for (int r = 0; r < kPC; ++r) *cl.map_shared_rank(&s_flag, r) = ok ? 1 : 0;
-    }
-    cl.sync();
-    if (!s_flag) break;
-    const JobArgs ja = pa.jobs[it.job];
-    const int4 item = make_int4(it.ltile, it.led, it.slot, 0);
-    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
-    if constexpr (MSEL == 64) {
-      run_update<P64, Img>(ja.u, item, smem);
-    } else if constexpr (MSEL == 128) {
-      run_update<P128, Img>(ja.u, item, smem);
-    } else if constexpr (MSEL == 192) {
-      run_update<P192, Img>(ja.u, item, smem);
-    } else if constexpr (MSEL == 256) {
-      run_update<P256, Img>(ja.u, item, smem);
-    } else {
-      switch (ja.m) {
-        case 64: run_update<P64, Img>(ja.u, item, smem); break;
-        case 128: run_update<P128, Img>(ja.u, item, smem); break;
-        case 192: run_update<P192, Img>(ja.u, item, smem); break;
-        default: run_update<P256, Img>(ja.u, item, smem); break;
+      if (load_acquire(&pa.err[1])) nidx = pa.n_items;
+      const PItem nit = nidx < pa.n_items ? pa.items[nidx] : PItem{};
+      for (int r = 0; r < kPC; ++r) {
+        *cl.map_shared_rank(&s_ok, r) = ok ? 1 : 0;
+        *cl.map_shared_rank(&s_idx[k ^ 1], r) = nidx;
+        *cl.map_shared_rank(&s_item[k ^ 1], r) = nit;
       }
     }
+    cl.sync();
+    if (!s_ok) break;
+    // job arguments are read through the pointer and the item re-read from
+    // shared memory after the update, so neither stays in registers across it
+    const JobArgs *jp = pa.jobs + s_item[k].job;
+    const int4 item = make_int4(s_item[k].ltile, s_item[k].led, s_item[k].slot, 0);
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    if constexpr (MSEL == 64) {
+      run_update<P64, Img>(jp->u, item, smem, load_tw);
+    } else if constexpr (MSEL == 128) {
+      run_update<P128, Img>(jp->u, item, smem, load_tw);
+    } else if constexpr (MSEL == 192) {
+      run_update<P192, Img>(jp->u, item, smem, load_tw);
+    } else if constexpr (MSEL == 256) {
+      run_update<P256x, Img>(jp->u, item, smem, load_tw);
+    } else {
+      switch (jp->m) {
+        case 64: run_update<P64, Img>(jp->u, item, smem, load_tw); break;
+        case 128: run_update<P128, Img>(jp->u, item, smem, load_tw); break;
+        case 192: run_update<P192, Img>(jp->u, item, smem, load_tw); break;
+        default: run_update<P256, Img>(jp->u, item, smem, load_tw); break;
+      }
+    }
+    const PItem done_it = s_item[k];
     // run_update ends with a cluster barrier: all of this update's writes are issued
     if (leader) {
       __threadfence();
-      const unsigned old = add_acq_rel(&pa.done[it.tile], 1u);
-      const int last = (old + 1u == (unsigned)it.target) ? 1 : 0;
-      for (int r = 0; r < kPC; ++r) *cl.map_shared_rank(&s_flag, r) = last;
+      const unsigned old = add_acq_rel(&pa.done[done_it.tile], 1u);
+      const int last = (old + 1u == (unsigned)done_it.target) ? 1 : 0;
+      for (int r = 0; r < kPC; ++r) *cl.map_shared_rank(&s_last, r) = last;
     }
     cl.sync();
-    if (s_flag) {          // this cluster completed the tile's wave: merge it, release the next
-      if (ja.epry)
-        merge_rows(const_cast<float2 *>(ja.u.pup), ja.u.dpup, ja.u.chords, it.ltile, it.width, (int)q, kPC,
-                   ja.u.y_lo, ja.u.rows, ja.m, ja.u.slots, threadIdx.x, blockDim.x);
+    if (s_last) {          // this cluster completed the tile's wave: merge it, release the next
+      const JobArgs *mj = pa.jobs + done_it.job;
+      if (mj->epry)
+        merge_rows(const_cast<float2 *>(mj->u.pup), mj->u.dpup, done_it.ltile, done_it.width, (int)q, kPC,
+                   mj->u.y_lo, mj->u.rows, mj->m, mj->u.slots, mj->u.disc, threadIdx.x, blockDim.x);
       __threadfence();
       cl.sync();
       if (leader) {
         __threadfence();
-        store_release(&pa.merged[it.tile], (unsigned)it.wave + 1u);
+        store_release(&pa.merged[done_it.tile], (unsigned)done_it.wave + 1u);
       }
     }
   }
@@ -267,15 +299,16 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
   std::vector<JobArgs> ja(jobs.size());
   size_t smem = 0;
   int msel = jobs[0].plan->m;
+  for (const QueueJob &j : jobs)
+    if (j.plan->m != msel) msel = 0;
   for (size_t j = 0; j < jobs.size(); ++j) {
     fpm_plan *p = jobs[j].plan;
-    if (p->m != msel) msel = 0;
     if (plan_image_dtype(p) != dtype) return fail(FPM_EINVAL, "jobs of one persistent run must share the image type");
     std::memset(&ja[j], 0, sizeof(JobArgs));
     ja[j].u = plan_update_args(p);
     ja[j].m = p->m;
     ja[j].epry = p->epry ? 1 : 0;
-    smem = std::max(smem, persistent_smem(p->m, p->y_hi - p->y_lo + 1));
+    smem = std::max(smem, persistent_smem(p->m, p->y_hi - p->y_lo + 1, msel));
   }
   if (smem > 232448) return fail(FPM_EINVAL, "a job's support is too large for the persistent kernel");
   const size_t n_items = items.size() / 8;
@@ -336,7 +369,7 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   }
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));
   cudaLaunchConfig_t cfg{};
-  cfg.blockDim = dim3(kPT, 1, 1);
+  cfg.blockDim = dim3(q->msel == 256 ? kPT256 : kPT, 1, 1);
   cfg.dynamicSmemBytes = q->smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

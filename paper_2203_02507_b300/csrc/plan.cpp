@@ -15,6 +15,7 @@
 #include <thread>
 
 #include "internal.h"
+#include "update_args.h"
 
 namespace fpm {
 
@@ -50,6 +51,16 @@ static void parallel_for(int64_t n, F f) {
       for (int64_t i = k; i < n; i += nt) f(i);
     });
   for (auto &t : th) t.join();
+}
+
+bool disc_bound_covers(int m, int32_t y_lo, int32_t y_hi, const int32_t *lo, const int32_t *hi) {
+  const int rows = y_hi - y_lo + 1;
+  for (int by = y_lo; by <= y_hi; ++by) {
+    const int hw = disc_half_width(by, y_lo, rows);
+    if (lo[by] > hi[by]) continue;
+    if (lo[by] < std::max(0, m / 2 - hw) || hi[by] > std::min(m - 1, m / 2 + hw)) return false;
+  }
+  return true;
 }
 
 int support_chords(int m, double df, double na, double wavelength_um, uint8_t *mask, int32_t *lo_v, int32_t *hi_v,
@@ -95,6 +106,7 @@ static bool build_support(fpm_plan *p) {
   p->chord_hi.assign(p->m, 0);
   const int c = support_chords(p->m, p->df, p->na, p->wavelength_um, p->support.data(), p->chord_lo.data(),
                                p->chord_hi.data(), &p->y_lo, &p->y_hi);
+  p->disc_ok = c > 0 && disc_bound_covers(p->m, p->y_lo, p->y_hi, p->chord_lo.data(), p->chord_hi.data());
   p->support_px = c > 0 ? c : 0;
   return c > 0;
 }

@@ -372,6 +372,7 @@ static UpdateArgs make_args(fpm_plan *p, const StepDev *sd) {
   a.y_lo = p->y_lo;
   a.rows = p->y_hi - p->y_lo + 1;
   a.slots = p->max_width;
+  a.disc = p->disc_ok ? 1 : 0;
   a.err = d->err;
   return a;
 }
@@ -421,10 +422,10 @@ int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long lo
   return FPM_OK;
 }
 
-int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, const int2 *chords, int y_lo,
-                 int rows, int m, int slots, cudaStream_t st) {
+int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, int y_lo, int rows, int m,
+                 int slots, int disc, cudaStream_t st) {
   if (count <= 0) return FPM_OK;
-  merge_kernel<<<dim3((unsigned)count, kNormParts), 256, 0, st>>>(pup, dpup, entries, chords, y_lo, rows, m, slots);
+  merge_kernel<<<dim3((unsigned)count, kNormParts), 256, 0, st>>>(pup, dpup, entries, y_lo, rows, m, slots, disc);
   FPM_CK(cudaGetLastError());
   return FPM_OK;
 }
@@ -474,8 +475,8 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
       }
       if (p->epry) {   // close the wave: its corrections into the pupils, in sequence order
         const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
-        if ((rc = launch_merge(d->pup, d->dpup, sd->merges + m0, (int)(m1 - m0), d->chords, p->y_lo, rows, p->m,
-                               p->max_width, st)))
+        if ((rc = launch_merge(d->pup, d->dpup, sd->merges + m0, (int)(m1 - m0), p->y_lo, rows, p->m,
+                               p->max_width, p->disc_ok ? 1 : 0, st)))
           return rc;
         if (m1 > m0) ++nl;
       }
@@ -503,8 +504,8 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
         if (p->epry) {
           for (long long k = sl.merge_off[s]; k < sl.merge_off[s + 1]; ++k)
             if (sl.merges[k * 2] == t) {
-              if ((rc = launch_merge(d->pup, d->dpup, sd->merges + k, 1, d->chords, p->y_lo, rows, p->m,
-                                     p->max_width, st)))
+              if ((rc = launch_merge(d->pup, d->dpup, sd->merges + k, 1, p->y_lo, rows, p->m,
+                                     p->max_width, p->disc_ok ? 1 : 0, st)))
                 return rc;
               ++nl;
             }

@@ -42,6 +42,6 @@ int plan_image_dtype(const fpm_plan *p);
 // The plan's device error word ([0] code, [1] abort flag), or null.
 unsigned *plan_error_word(fpm_plan *p);
 // Launch the pupil merge over `count` (tile, slots) entries.
-int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, const int2 *chords, int y_lo,
-                 int rows, int m, int slots, cudaStream_t st);
+int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, int y_lo, int rows, int m,
+                 int slots, int disc, cudaStream_t st);
 }  // namespace fpm

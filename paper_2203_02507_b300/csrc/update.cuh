@@ -77,9 +77,11 @@ struct ImgCol {
   }
 };
 
-template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1>
+// PF_ = 1: a lane loads its next column's image pixels one column ahead;
+// 0: at the start of the column (8 registers fewer for 16-bit images, 16 for float).
+template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1>
 struct UpdateCfg {
-  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_;
+  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_;
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -96,17 +98,29 @@ struct UpdateCfg {
   }
 };
 
+// The transform twiddles of tile side M into the start of shared memory (the
+// caller synchronises before run_update reads them).
+template <class Cfg>
+__device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem) {
+  for (int i = threadIdx.x; i < Cfg::M; i += Cfg::T) {
+    smem[i] = a.tw_inv[i];
+    smem[Cfg::M + i] = a.tw_fwd[i];
+  }
+}
+
 // One update; all threads of all C CTAs of the cluster call this with the same item.
+// Shared memory: [twiddles 2m][normaliser partials][inter R x W][exchange scratch].
+// load_tw = false keeps the twiddles of an earlier update with the same m.
 template <class Cfg, typename Img>
-__device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem) {
+__device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem, bool load_tw = true) {
   constexpr int M = Cfg::M, A = Cfg::A, B = Cfg::B, TPT = Cfg::TPT, C = Cfg::C, T = Cfg::T;
   constexpr int W = Cfg::W, G = Cfg::G, SCR = Cfg::SCR;
   const int rows = a.rows;
-  float2 *inter = smem;
-  float2 *scratch_all = inter + (size_t)rows * W;
-  float2 *twi = scratch_all + G * SCR;
+  float2 *twi = smem;
   float2 *twf = twi + M;
   float *red = reinterpret_cast<float *>(twf + M);
+  float2 *inter = twf + M + 32;             // after 64 floats of partials
+  float2 *scratch_all = inter + (size_t)rows * W;
 
   const int tid = threadIdx.x;
   const int g = tid / TPT, tl = tid % TPT;
@@ -137,15 +151,12 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const Img *img = reinterpret_cast<const Img *>(a.images) + tile_image_offset(tile, led, a.n_leds, M) +
                    (size_t)q * W * M;
 
-  for (int i = tid; i < M; i += T) {
-    twi[i] = a.tw_inv[i];
-    twf[i] = a.tw_fwd[i];
-  }
-  __syncthreads();
-
   // rows of the support handled by this CTA in phases 1 and 3
   const int rpc = (rows + C - 1) / C;
   const int r0 = q * rpc, r1 = min(rows, r0 + rpc);
+
+  if (load_tw) load_twiddles<Cfg>(a, smem);
+  __syncthreads();
 
   // ---- phase 1: IDFT along x of every support row -------------------------
   float omax = 0.f, pmax = 0.f;
@@ -215,6 +226,22 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   } else {
     __syncthreads();
   }
+  // the last warp (whose groups have the fewest columns in phase 2) combines
+  // the cluster's partials while the others start phase 2; phase 3 reads the
+  // result after the phase 2 barrier
+  if (tid >= T - 32) {
+    const int l = tid - (T - 32), wi = l & 15;
+    float v = (wi < T / 32) ? red[l] : 0.f;            // lanes 0-15: |O|^2, 16-31: |P|^2
+    if constexpr (C > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      for (int r = 0; r < C; ++r)
+        if (r != q && wi < T / 32) v = fmaxf(v, cl.map_shared_rank(red, r)[l]);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (l == 0) red[32] = v;
+    if (l == 16) red[33] = v;
+  }
 
   // ---- phase 2: columns: IDFT along y, amplitude step, DFT along y ---------
   const int y_lo = a.y_lo, y_hi = a.y_lo + rows - 1;
@@ -236,7 +263,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       if (b < B && y >= y_lo && y <= y_hi) out_mask[u] |= 1u << k2;
     }
   }
-  // measured pixels of this lane's rows y = k1 + A k2 (B contiguous elements), one column ahead
+  // measured pixels of this lane's rows y = k1 + A k2 (B contiguous elements)
   ImgCol<Img, B> meas[Cfg::UB];
   auto fetch = [&](int col, ImgCol<Img, B> (&dst)[Cfg::UB]) {
 #pragma unroll
@@ -246,10 +273,11 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       else dst[u].zero();
     }
   };
-  fetch(g, meas);
+  if constexpr (Cfg::PF) fetch(g, meas);
   for (int c = g; c < W; c += G) {
-    ImgCol<Img, B> next[Cfg::UB];
-    fetch(c + G, next);
+    ImgCol<Img, B> next[Cfg::PF ? Cfg::UB : 1];
+    if constexpr (Cfg::PF) fetch(c + G, next);
+    else fetch(c, meas);                   // consumed after the first pass
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int b = tl + u * TPT;
@@ -328,7 +356,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
     }
     __syncwarp(gmask);
 #pragma unroll
-    for (int u = 0; u < Cfg::UB; ++u) meas[u] = next[u];
+    for (int u = 0; u < Cfg::UB; ++u)
+      if constexpr (Cfg::PF) meas[u] = next[u];
   }
   if constexpr (C > 1) {
     cg::this_cluster().sync();
@@ -336,21 +365,6 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
     __syncthreads();
   }
 
-  // normalisers
-  if (tid < 32) {
-    const int wi = tid & 15;
-    float v = (wi < T / 32) ? red[tid] : 0.f;          // lanes 0-15: |O|^2, 16-31: |P|^2
-    if constexpr (C > 1) {
-      cg::cluster_group cl = cg::this_cluster();
-      for (int r = 0; r < C; ++r)
-        if (r != q && wi < T / 32) v = fmaxf(v, cl.map_shared_rank(red, r)[tid]);
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (tid == 0) red[32] = v;
-    if (tid == 16) red[33] = v;
-  }
-  __syncthreads();
   const float onorm = red[32], pn = red[33];
   const float inv_on = (onorm > 0.f) ? 1.f / onorm : 0.f;
   const float inv_pn = 1.f / pn;

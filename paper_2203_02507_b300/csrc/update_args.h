@@ -13,6 +13,23 @@ constexpr int kNormParts = 8;
 // column x position k1 * B + k2 holds row y = k1 + A * k2, the order in which
 // the radix-B pass of the column transform consumes it.  One lane's B pixels
 // are then contiguous.
+// Half-width bound of the support disc in box row by (support rows y_lo ..
+// y_lo + rows - 1, centre column m/2): the support's chord in that row lies in
+// [m/2 - hw, m/2 + hw].  With rows = 2 floor(r) + 1 for a disc of radius r,
+// r < (rows + 1) / 2, so hw = floor(sqrt(((rows + 1)/2)^2 - dy^2)) + 1 bounds
+// the chord; plans verify it against their chords (disc_bound_covers).  Every
+// step is exact in float or correctly rounded, so host and device agree.
+__host__ __device__ inline int disc_half_width(int by, int y_lo, int rows) {
+  const float rr = 0.5f * (float)(rows + 1);
+  const float dy = (float)by - ((float)y_lo + 0.5f * (float)(rows - 1));
+#ifdef __CUDA_ARCH__
+  const float h2 = __fsub_rn(__fmul_rn(rr, rr), __fmul_rn(dy, dy));
+#else
+  const float h2 = rr * rr - dy * dy;
+#endif
+  return (int)sqrtf(h2 > 0.f ? h2 : 0.f) + 1;
+}
+
 // The split of each supported tile side; every kernel for that side uses it.
 constexpr int image_split_a(int m) { return m == 64 ? 8 : m == 128 ? 16 : m == 192 ? 12 : m == 256 ? 16 : 0; }
 __host__ __device__ inline size_t tile_image_offset(int t, int l, int n_leds, int m) {
@@ -36,6 +53,7 @@ struct UpdateArgs {
   int y_lo;                   // first support row (box coordinates)
   int rows;                   // R
   int slots;                  // correction slots per tile
+  int disc;                   // 1: disc_half_width bounds every support chord
   unsigned *err;
 };
 
