@@ -251,6 +251,10 @@ typedef struct {
   int32_t device_error;     /* 0, or FPM_ETIMEOUT if a bounded device wait of the last
                                persistent run gave up                                   */
   int32_t persistent_clusters; /* clusters of the last persistent launch               */
+  int32_t run_threads;      /* threads per CTA of the update kernel the last
+                               fpm_reconstruct ran (a graph replay: the variant it was
+                               captured with; persistent: the persistent kernel's)     */
+  int32_t pad0;
 } fpm_stats;
 
 /* fpm_get_stats -- fill *out.  Synchronises the device; update_ms is 0 when no
@@ -361,6 +365,17 @@ FPM_API int fpm_server_destroy(fpm_server *server);
 FPM_API int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32_t m, const float *image,
                                    int32_t shift_y, int32_t shift_x, double wavelength_um, double na,
                                    double pixel_um, int32_t epry, void *stream);
+
+/*
+ * fpm_fp32_peak -- measured FP32 throughput of the current device, the
+ * denominator of the update kernel's roofline (its bound is FP32 arithmetic).
+ * Times chains of fused multiply-adds that keep every FP32 lane busy (eight
+ * independent chains per thread, 2048 threads per SM) at the clocks the device
+ * runs at, and writes the best of three timed launches, in TFLOP/s (2 flop per
+ * FMA), to *tflops.  Takes ~10 ms and 1 KB of device memory; synchronises the
+ * stream.  FPM_ECUDA on a CUDA failure.
+ */
+FPM_API int fpm_fp32_peak(double *tflops, void *stream);
 
 /* fpm_last_error -- text of the calling thread's last failure ("" if none). */
 FPM_API const char *fpm_last_error(void);

@@ -4,7 +4,8 @@ The binding is loaded on first use of any of its names; that import fails when
 libfpm.so has not been built (there is no CPU fallback).  Build it with
 ``python -m paper_2203_02507_b300.build``.
 """
-_NAMES = ("EXPORTED", "FpmError", "Plan", "Server", "plan_for", "update_tile_static", "reconstruct_batch", "LIB_PATH")
+_NAMES = ("EXPORTED", "FpmError", "Plan", "Server", "plan_for", "update_tile_static", "reconstruct_batch", "fp32_peak",
+          "LIB_PATH")
 
 
 def __getattr__(name):

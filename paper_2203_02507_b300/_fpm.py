@@ -68,7 +68,7 @@ class TuneEntry(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
                 ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
-                ("persistent_clusters", C.c_int32)]
+                ("persistent_clusters", C.c_int32), ("run_threads", C.c_int32), ("pad0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +95,7 @@ _SIGS = {
     "fpm_server_destroy": [_vp],
     "fpm_reconstruct_batch": [C.POINTER(_vp), C.POINTER(_i32), _i32, _i32, _vp],
     "fpm_update_tile_static": [_vp, _i32, _vp, _i32, _vp, _i32, _i32, C.c_double, C.c_double, C.c_double, _i32, _vp],
+    "fpm_fp32_peak": [C.POINTER(C.c_double), _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -215,9 +216,11 @@ class Plan:
                 | (RUN_FAULT_TEST if fault_test else 0))
         _check(_lib.fpm_reconstruct(self._h, int(iters or self.iters), flag, _stream(stream)))
 
-    def autotune(self, iters: int = 1, stream=None):
-        """Time every execution path on `iters` loops of the loaded data and keep the
-        fastest (for mode="auto"); returns ([{mode, threads, cluster, ms}], best index)."""
+    def autotune(self, iters: int | None = None, stream=None):
+        """Time every execution path on `iters` loops (default: the plan's loop count)
+        of the loaded data and keep the fastest (for mode="auto"); returns
+        ([{mode, threads, cluster, ms}], best index)."""
+        iters = self.info["iters"] if iters is None else iters
         ent = (TuneEntry * 16)()
         n, best = _i32(), _i32()
         _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, 16, C.byref(n), C.byref(best)))
@@ -324,6 +327,13 @@ def update_tile_static(spectrum, pupil, image, shift, wavelength_um, na, pixel_u
     _check(_lib.fpm_update_tile_static(_ptr(spectrum), n, _ptr(pupil), m, _ptr(image), int(shift[0]),
                                        int(shift[1]), float(wavelength_um), float(na), float(pixel_um),
                                        1 if epry else 0, _stream(stream)))
+
+
+def fp32_peak(stream=None) -> float:
+    """Measured FP32 throughput of the current device in TFLOP/s (fpm_fp32_peak)."""
+    v = C.c_double(0.0)
+    _check(_lib.fpm_fp32_peak(C.byref(v), _stream(stream)))
+    return v.value
 
 
 def plan_for(workload, defocus_um=None, iters=None) -> Plan:

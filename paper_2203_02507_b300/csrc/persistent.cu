@@ -343,6 +343,8 @@ int make_queue(const std::vector<QueueJob> &jobs, QueueDev **out) {
 
 int queue_items(const QueueDev *q) { return q ? q->n_items : 0; }
 
+int persistent_block_threads(int m) { return m == 256 ? kPT256 : kPT; }
+
 int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, int *clusters_out) {
   if (q->n_items == 0) return FPM_OK;
   FPM_CK(cudaMemsetAsync(q->counters, 0, (1 + 2 * (size_t)q->n_tiles) * 4, st));
@@ -369,7 +371,7 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   }
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));
   cudaLaunchConfig_t cfg{};
-  cfg.blockDim = dim3(q->msel == 256 ? kPT256 : kPT, 1, 1);
+  cfg.blockDim = dim3(persistent_block_threads(q->msel), 1, 1);
   cfg.dynamicSmemBytes = q->smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

@@ -180,6 +180,8 @@ struct DeviceState {
   std::vector<StepDev> steps;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, int64_t> graph_launches;
+  std::map<GraphKey, int32_t> graph_threads;      // update-kernel threads captured in each graph
+  int32_t run_threads = 0;                        // of the last fpm_reconstruct (fpm_get_stats)
   // counters (fpm_get_stats)
   int64_t load_launches = 0, run_launches = 0;
   std::vector<cudaEvent_t> events;            // 2 per wave step of a timed run
@@ -674,6 +676,7 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
   out->load_launches = d->load_launches;
   out->run_launches = d->run_launches;
   out->persistent_clusters = d->persistent_clusters;
+  out->run_threads = d->run_threads;
   const int derr = device_error(p);
   out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
   if (d->timed_valid && !d->timed_steps.empty()) {
@@ -826,11 +829,15 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   if (stall && base != FPM_RUN_PERSISTENT) return fail(FPM_EINVAL, "FPM_RUN_FAULT_TEST needs FPM_RUN_PERSISTENT");
   cudaStream_t st = (cudaStream_t)stream;
   fpm::DeviceState *d = p->dev;
-  if (base == FPM_RUN_PERSISTENT) return fpm::run_persistent(p, iters, st, graph, stall);
+  if (base == FPM_RUN_PERSISTENT) {
+    d->run_threads = fpm::persistent_block_threads(p->m);
+    return fpm::run_persistent(p, iters, st, graph, stall);
+  }
   if (!graph) {
     int64_t nl = 0;
     int rc = fpm::enqueue_reconstruct(p, iters, base, st, timed, false, &nl);
     d->run_launches = nl;
+    d->run_threads = d->var->t;
     return rc;
   }
   fpm::GraphKey key{iters, mode & 0xfff, st};
@@ -850,6 +857,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     int64_t nl = 0;
     rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
     d->graph_launches[key] = nl;
+    d->graph_threads[key] = d->var->t;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (own) cudaStreamDestroy(cap);
@@ -878,6 +886,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   }
   FPM_CK(cudaGraphLaunch(it->second, st));
   d->run_launches = d->graph_launches[key];
+  d->run_threads = d->graph_threads[key];
   return FPM_OK;
 }
 
@@ -959,17 +968,18 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
     int bw = -1;
     for (size_t i = 0; i < cands.size(); ++i)
       if (cands[i].v && (bw < 0 || cands[i].ms < cands[bw].ms)) bw = (int)i;
-    if (bw >= 0 && d->var != cands[bw].v) {
-      d->var = cands[bw].v;
-      for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
-      d->graphs.clear();
-    }
+    if (bw >= 0) d->var = cands[bw].v;
     d->tuned_mode = cands[bi].mode;
     p->cluster = d->var->c;
     p->threads = d->var->t;
   } else {
     d->var = keep;
   }
+  // the candidates' wave graphs share one cache key: whichever ran last must not
+  // outlive the tuning, so the chosen variant's graph is captured on next use
+  cudaStreamSynchronize(st);
+  for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
+  d->graphs.clear();
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
@@ -980,7 +990,7 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
     for (int i = 0; i < (int)cands.size() && i < max_entries; ++i) {
       const auto &c = cands[i];
       entries[i].mode = c.mode;
-      entries[i].threads = c.v ? c.v->t : 384;
+      entries[i].threads = c.v ? c.v->t : fpm::persistent_block_threads(p->m);
       entries[i].cluster = c.v ? c.v->c : 2;
       entries[i].ms = c.ms;
     }

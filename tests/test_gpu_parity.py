@@ -252,6 +252,8 @@ def test_autotune_keeps_state_and_picks_a_bit_identical_path():
     for t in range(j.w.n_tiles):                        # the trials left the state as it was
         assert np.array_equal(p.spectrum(t), before[t])
     p.reconstruct(2, mode="auto", graph=True)
+    chosen = entries[best]
+    assert p.stats()["run_threads"] == chosen["threads"]          # the chosen path runs, not a trial's graph
     auto = [p.spectrum(t) for t in range(j.w.n_tiles)] + [p.pupil(t) for t in range(j.w.n_tiles)]
     q = j.plan(iters=2)
     q.load_tiles(j.stack, j.counts_per_unit)
@@ -259,5 +261,22 @@ def test_autotune_keeps_state_and_picks_a_bit_identical_path():
     ref = [q.spectrum(t) for t in range(j.w.n_tiles)] + [q.pupil(t) for t in range(j.w.n_tiles)]
     for a, b in zip(auto, ref):
         assert np.array_equal(a, b)
+    # wave launches after tuning use the fastest wave variant
+    fastest_waves = min((e for e in entries if e["mode"] == "waves"), key=lambda e: e["ms"])
+    p.reconstruct(1, mode="waves", graph=True)
+    assert p.stats()["run_threads"] == fastest_waves["threads"]
     p.close()
     q.close()
+    q.close()
+
+
+def test_fp32_peak_is_near_the_nominal_rate():
+    """The roofline denominator: measured FFMA throughput lies between half the
+    nominal rate at the device's maximum clock and a little above it."""
+    import torch
+    from paper_2203_02507_b300 import fp32_peak
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    nominal = sms * 128 * 2 * 2.032e9 / 1e12        # 128 FP32 lanes per SM, 2 flop per FMA
+    v = fp32_peak()
+    assert 0.5 * nominal < v < 1.05 * nominal, (v, nominal)
