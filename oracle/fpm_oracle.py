@@ -21,6 +21,8 @@ choice the paper leaves open is a stated reading:
                     Opt. Express 22(5):4960 (2014), alpha = beta = 1
   waves             Sec. 3.2 (regions that do not affect one another updated
                     in parallel, across iteration loops)
+  stitching         Sec. 3.1, Eq. 1 (pairwise, weights mu1/mu2 read as the
+                    complex means over the shared band)
 
 Parity status: every function below is pinned by the CPU tests in
 ``tests/test_oracle_*.py`` (brute-force DFT, closed-form images, the fixed-point
@@ -367,3 +369,69 @@ def tile_images_from_stack(stack, origin, m, counts_per_unit=1.0):
 def object_from_spectrum(spectrum):
     """HR complex object o = ifft2c(O)."""
     return ifft2c(spectrum)
+
+
+# ---------------------------------------------------------------------------
+# Stitching of the tile objects into one HR field of view (Eq. 1, Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def hr_overlap(overlap, upsample):
+    """Lines shared by neighbouring tile objects on the HR grid.
+
+    Reading: tiles are cut on the LR sensor with `overlap` shared pixels and
+    each tile's object lives on a grid `upsample` times finer, so neighbouring
+    objects share overlap * upsample lines.  (The paper's example, 256 x 256
+    images sharing 26 lines, gives sizes in one pixel grid only.)
+    """
+    return int(overlap) * int(upsample)
+
+
+def stitch_pair(f1, f2, overlap, axis):
+    """Eq. 1 for one pair: f2 continues f1 along `axis`, the two sharing `overlap` lines.
+
+    axis 0 is the paper's part 1 (f2 below f1, the condition on the row index
+    x), axis 1 its part 2 (f2 right of f1, the condition on the column index y).
+    With r lines in f1, output line i < r - overlap/2 is f1's line i; every
+    later output line i is (mu1 / mu2) times f2's line i - (r - overlap), so the
+    output has r + r2 - overlap lines.  overlap/2 is taken as overlap // 2.
+
+    Reading of the weights: mu1 and mu2 are the complex means of f1 and f2 over
+    the band both images cover (f1's last `overlap` lines, f2's first), the
+    only region in which their ratio compares the same part of the sample.  A
+    zero mu2 leaves f2 unscaled.
+    """
+    a = np.moveaxis(np.asarray(f1, dtype=np.complex128), axis, 0)
+    b = np.moveaxis(np.asarray(f2, dtype=np.complex128), axis, 0)
+    if a.shape[1:] != b.shape[1:]:
+        raise ValueError("the images must agree across the stitching axis")
+    r, r2 = a.shape[0], b.shape[0]
+    if overlap < 1 or overlap > min(r, r2):
+        raise ValueError("overlap out of range")
+    mu1 = np.ascontiguousarray(a[r - overlap:]).mean()     # contiguous copies: one summation
+    mu2 = np.ascontiguousarray(b[:overlap]).mean()         # order for both bands
+    w = mu1 / mu2 if mu2 != 0 else 1.0
+    cut = r - overlap // 2
+    out = np.empty((r + r2 - overlap,) + a.shape[1:], dtype=np.complex128)
+    out[:cut] = a[:cut]
+    out[cut:] = w * b[cut - (r - overlap):]
+    return np.moveaxis(out, 0, axis)
+
+
+def stitch_grid(objects, tiles_y, tiles_x, overlap):
+    """One field-of-view image from the tile objects (Eq. 1, Sec. 3.1).
+
+    objects[i * tiles_x + j] is the object of the tile in grid row i, column j.
+    Each column of tiles is stitched top to bottom (part 1), the running result
+    being f1 of the next stitch; the column images are then stitched left to
+    right the same way (part 2), the paper's part-1 output being part 2's input.
+    """
+    strips = []
+    for j in range(tiles_x):
+        s = np.asarray(objects[j], dtype=np.complex128)
+        for i in range(1, tiles_y):
+            s = stitch_pair(s, objects[i * tiles_x + j], overlap, 0)
+        strips.append(s)
+    out = strips[0]
+    for j in range(1, tiles_x):
+        out = stitch_pair(out, strips[j], overlap, 1)
+    return out
