@@ -280,6 +280,40 @@ def aggregate(ms_local, updates_local, dist=None, device=None):
 # batched and served forms
 # ---------------------------------------------------------------------------
 
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json, copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def stitch_timing(plan, torch, dev, stack, k, w, reps=3):
+    """fpm_stitch of the reconstructed FOV into a device image (Eq. 1): device time and
+    bandwidth on its algorithmic bytes (every spectrum read once, the image written once)."""
+    plan.load_tiles(stack, k)
+    plan.reconstruct(1, mode="waves", graph=True)
+    info = plan.info
+    out = torch.empty((info["fov_h"], info["fov_w"]), dtype=torch.complex64, device=dev)
+    plan.stitch(out=out)                                   # warm-up
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        plan.stitch(out=out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = w.n_tiles * w.hr * w.hr * 8 + info["fov_h"] * info["fov_w"] * 8
+    peak, src = hbm_peak_gbs()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"ms": ms, "fov": [info["fov_h"], info["fov_w"]], "hr_overlap": info["hr_overlap"],
+            "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_peak_gbs": peak, "frac": gbs / peak, "peak_source": src,
+            "includes": "per-tile N x N inverse FFTs (line FFT kernel), band sums, assembly; temporaries allocated "
+                        "stream-ordered"}
+
+
 def uneven_batch(torch, dev, steps=3):
     """Three jobs (128/192/256 tiles, 9x9/13x13/15x15 LEDs, 15 loops, EPRY) in one
     persistent launch per step; returns updates/s and ms per step."""
@@ -567,6 +601,7 @@ def main():
                                     "share_of_step": s2["update_ms"] / pms}
         line[other + "_path"] = alt
         del host_stack, host_out
+        line["stitch"] = stitch_timing(plan, torch, dev, stack, k, w)
         line["uneven_batch"] = uneven_batch(torch, dev)
         if args.serving_jobs > 0:
             line["serving"] = serving(torch, dev, args.serving_jobs)

@@ -126,6 +126,9 @@ typedef struct {
   int32_t threads;              /* threads per CTA of the update kernel                */
   int64_t image_elems;          /* elements of the tile images fpm_load_tiles keeps
                                    (n_tiles * n_leds * m * m, each of the stack's type) */
+  int32_t hr_overlap;           /* lines neighbouring tile objects share: overlap * (N/m) */
+  int32_t fov_h, fov_w;         /* size of fpm_stitch's image: N + (tiles - 1)(N - hr_overlap) */
+  int32_t pad0;
 } fpm_plan_info;
 
 /*
@@ -376,6 +379,32 @@ FPM_API int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32
  * stream.  FPM_ECUDA on a CUDA failure.
  */
 FPM_API int fpm_fp32_peak(double *tflops, void *stream);
+
+/*
+ * fpm_get_object -- the tile's HR complex object o = IDFT_N(ifftshift(O)) with
+ * the 1/N^2 factor, O its current centred spectrum: N x N complex64,
+ * row-major, written to dst (device memory if on_device, else host memory and
+ * the call synchronises).  Computed on the device from the spectrum (line FFTs
+ * along rows and columns).  FPM_ESTATE before fpm_load_tiles; FPM_ETIMEOUT (host
+ * copies) if the last persistent run's bounded wait gave up.
+ */
+FPM_API int fpm_get_object(fpm_plan *plan, int32_t tile, void *dst, int32_t on_device, void *stream);
+
+/*
+ * fpm_stitch -- the whole field of view as one HR complex image (Eq. 1,
+ * Sec. 3.1): fov_h x fov_w complex64, row-major (sizes in fpm_plan_info),
+ * written to dst (device memory if on_device, else host memory and the call
+ * synchronises).  Every tile's object (fpm_get_object) is placed at
+ * (i, j) * (N - hr_overlap); the tiles of each grid column are stitched top
+ * to bottom, then the columns left to right, each pair as Eq. 1: lines before
+ * r - hr_overlap/2 (integer division) of the running image are kept, the rest
+ * come from the next image times mu1/mu2.  Reading: mu1 and mu2 are the complex
+ * means of the two images over the hr_overlap lines both cover; a zero mu2, or
+ * hr_overlap 0, gives weight 1.  Device temporaries: n_tiles * N^2 * 8 bytes of
+ * objects (plus the image itself for a host dst).  FPM_EINVAL if hr_overlap >
+ * N/2; FPM_ENOMEM; FPM_ESTATE before fpm_load_tiles.
+ */
+FPM_API int fpm_stitch(fpm_plan *plan, void *dst, int32_t on_device, void *stream);
 
 /* fpm_last_error -- text of the calling thread's last failure ("" if none). */
 FPM_API const char *fpm_last_error(void);

@@ -398,18 +398,21 @@ def stitch_pair(f1, f2, overlap, axis):
     Reading of the weights: mu1 and mu2 are the complex means of f1 and f2 over
     the band both images cover (f1's last `overlap` lines, f2's first), the
     only region in which their ratio compares the same part of the sample.  A
-    zero mu2 leaves f2 unscaled.
+    zero mu2 leaves f2 unscaled, and so does overlap 0 (no shared band: the
+    images are placed side by side).
     """
     a = np.moveaxis(np.asarray(f1, dtype=np.complex128), axis, 0)
     b = np.moveaxis(np.asarray(f2, dtype=np.complex128), axis, 0)
     if a.shape[1:] != b.shape[1:]:
         raise ValueError("the images must agree across the stitching axis")
     r, r2 = a.shape[0], b.shape[0]
-    if overlap < 1 or overlap > min(r, r2):
+    if overlap < 0 or overlap > min(r, r2):
         raise ValueError("overlap out of range")
-    mu1 = np.ascontiguousarray(a[r - overlap:]).mean()     # contiguous copies: one summation
-    mu2 = np.ascontiguousarray(b[:overlap]).mean()         # order for both bands
-    w = mu1 / mu2 if mu2 != 0 else 1.0
+    w = 1.0
+    if overlap > 0:
+        mu1 = np.ascontiguousarray(a[r - overlap:]).mean()     # contiguous copies: one summation
+        mu2 = np.ascontiguousarray(b[:overlap]).mean()         # order for both bands
+        w = mu1 / mu2 if mu2 != 0 else 1.0
     cut = r - overlap // 2
     out = np.empty((r + r2 - overlap,) + a.shape[1:], dtype=np.complex128)
     out[:cut] = a[:cut]

@@ -54,7 +54,8 @@ class PlanInfo(C.Structure):
         ("iters", C.c_int32), ("support_px", C.c_int32), ("support_rows", C.c_int32),
         ("max_waves", C.c_int32), ("max_wave_width", C.c_int32), ("total_waves", C.c_int64),
         ("device_bytes", C.c_int64), ("cluster", C.c_int32), ("threads", C.c_int32),
-        ("image_elems", C.c_int64),
+        ("image_elems", C.c_int64), ("hr_overlap", C.c_int32), ("fov_h", C.c_int32), ("fov_w", C.c_int32),
+        ("pad0", C.c_int32),
     ]
 
     def as_dict(self):
@@ -96,6 +97,8 @@ _SIGS = {
     "fpm_reconstruct_batch": [C.POINTER(_vp), C.POINTER(_i32), _i32, _i32, _vp],
     "fpm_update_tile_static": [_vp, _i32, _vp, _i32, _vp, _i32, _i32, C.c_double, C.c_double, C.c_double, _i32, _vp],
     "fpm_fp32_peak": [C.POINTER(C.c_double), _vp],
+    "fpm_get_object": [_vp, _i32, _vp, _i32, _vp],
+    "fpm_stitch": [_vp, _vp, _i32, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -245,6 +248,20 @@ class Plan:
         if out is None:
             out = np.zeros((self.m, self.m), np.complex64)
         _check(_lib.fpm_get_pupil(self._h, int(tile), _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
+        return out
+
+    def object(self, tile: int, out=None, stream=None):
+        """The tile's HR complex object (fpm_get_object)."""
+        if out is None:
+            out = np.zeros((self.n, self.n), np.complex64)
+        _check(_lib.fpm_get_object(self._h, int(tile), _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
+        return out
+
+    def stitch(self, out=None, stream=None):
+        """The whole field of view as one HR complex image (fpm_stitch, Eq. 1)."""
+        if out is None:
+            out = np.zeros((self.info["fov_h"], self.info["fov_w"]), np.complex64)
+        _check(_lib.fpm_stitch(self._h, _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
         return out
 
     def set_state(self, tile: int, spectrum=None, pupil=None, stream=None):

@@ -417,6 +417,9 @@ int fpm_plan_get_info(const fpm_plan *p, fpm_plan_info *info) {
   info->cluster = p->cluster;
   info->threads = p->threads;
   info->image_elems = T * p->n_leds * m * m;
+  info->hr_overlap = p->overlap * p->upsample;
+  info->fov_h = (int32_t)(n + (p->tiles_y - 1) * (n - info->hr_overlap));
+  info->fov_w = (int32_t)(n + (p->tiles_x - 1) * (n - info->hr_overlap));
   return FPM_OK;
 }
 

@@ -113,7 +113,7 @@ void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd) {
     }
 }
 
-static std::vector<float2> twiddles_line(int len, int sign) {
+std::vector<float2> twiddles_line(int len, int sign) {
   std::vector<float2> t(len);
   for (int j = 0; j < len; ++j) {
     const double ang = sign * 2.0 * M_PI * (double)j / len;
@@ -437,6 +437,8 @@ UpdateArgs plan_update_args(fpm_plan *p) { return make_args(p, nullptr); }
 int plan_image_dtype(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->dtype : -1; }
 
 unsigned *plan_error_word(fpm_plan *p) { return p->dev ? p->dev->err : nullptr; }
+
+const float2 *plan_spectra(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->spec : nullptr; }
 
 // Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
 // With `timed`, CUDA events bracket every update launch (waves mode only).

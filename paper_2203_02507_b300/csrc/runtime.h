@@ -8,6 +8,8 @@
 #include "update_args.h"
 
 namespace fpm {
+// Twiddle table of the line FFT: exp(sign 2 pi i j / len), j < len.
+std::vector<float2> twiddles_line(int len, int sign);
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
                      long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st);
 struct QueueJob;
@@ -41,6 +43,8 @@ UpdateArgs plan_update_args(fpm_plan *p);
 int plan_image_dtype(const fpm_plan *p);
 // The plan's device error word ([0] code, [1] abort flag), or null.
 unsigned *plan_error_word(fpm_plan *p);
+// The plan's spectra [T][N][N] (centred complex64) once loaded, else null.
+const float2 *plan_spectra(const fpm_plan *p);
 // Launch the pupil merge over `count` (tile, slots) entries.
 int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, int y_lo, int rows, int m,
                  int slots, int disc, cudaStream_t st);

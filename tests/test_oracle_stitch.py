@@ -32,7 +32,7 @@ def test_paper_worked_sizes():
     assert g["overlap"] == round(0.1 * g["image"][0])
 
 
-@pytest.mark.parametrize("ty,tx,n,ov", [(2, 2, 32, 8), (3, 4, 24, 6), (1, 3, 16, 5), (3, 1, 20, 7)])
+@pytest.mark.parametrize("ty,tx,n,ov", [(2, 2, 32, 8), (3, 4, 24, 6), (1, 3, 16, 5), (3, 1, 20, 7), (2, 3, 16, 0)])
 def test_windows_of_one_image_reassemble_exactly(ty, tx, n, ov):
     h, w = n + (ty - 1) * (n - ov), n + (tx - 1) * (n - ov)
     img = _field(h, w, 7)
