@@ -401,8 +401,9 @@ FPM_API int fpm_get_object(fpm_plan *plan, int32_t tile, void *dst, int32_t on_d
  * come from the next image times mu1/mu2.  Reading: mu1 and mu2 are the complex
  * means of the two images over the hr_overlap lines both cover; a zero mu2, or
  * hr_overlap 0, gives weight 1.  Device temporaries: n_tiles * N^2 * 8 bytes of
- * objects (plus the image itself for a host dst).  FPM_EINVAL if hr_overlap >
- * N/2; FPM_ENOMEM; FPM_ESTATE before fpm_load_tiles.
+ * objects (plus the image itself for a host dst), kept with the plan for later
+ * calls and freed by fpm_plan_destroy.  FPM_EINVAL if hr_overlap > N/2;
+ * FPM_ENOMEM; FPM_ESTATE before fpm_load_tiles.
  */
 FPM_API int fpm_stitch(fpm_plan *plan, void *dst, int32_t on_device, void *stream);
 

@@ -17,7 +17,8 @@ constexpr int kMaxFftLen = 2048;
 constexpr int kMaxRadices = 12;
 
 struct FftLines {
-  float2 *data;
+  float2 *data;                // output lines (and input, unless src is set)
+  const float2 *src;           // input lines at the same offsets, or null (in place)
   const float2 *tw;            // [len] exp(sign 2 pi i j / len)
   long long batch_stride;      // elements between batches
   long long line_stride;       // elements between lines of a batch
@@ -26,48 +27,84 @@ struct FftLines {
   int len;
   int nrad;
   int radix[kMaxRadices];
+  int lines_per_cta;           // 1, or that many adjacent lines (line_stride 1), moved
+                               // together so each 32-byte sector is used whole
+  float finish;                // 0, or: output (e, l) times finish * (-1)^(e + l),
+                               // e the sample and l the line index within its batch
 };
 
-// Stockham pass: R-point butterflies on strided inputs, autosorted outputs.
+// Shared-memory position of line sample i: one pad slot per 16 samples, so a
+// butterfly's R outputs written with unit stride by consecutive threads (the
+// first Stockham pass) fall in different banks.
+__device__ __forceinline__ int line_pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int line_padded_len(int len) { return len + len / 16 + 1; }
+
+// Stockham pass: R-point butterflies on strided inputs, autosorted outputs,
+// butterflies j = t, t + nt, ... done by threads t of a group of nt.
 template <int R, int S>
-__device__ __forceinline__ void stockham_pass(const float2 *x, float2 *y, const float2 *tw, int len, int ns) {
+__device__ __forceinline__ void stockham_pass(const float2 *x, float2 *y, const float2 *tw, int len, int ns, int t,
+                                              int nt) {
   const int span = len / R;
-  for (int j = threadIdx.x; j < span; j += blockDim.x) {
+  for (int j = t; j < span; j += nt) {
     const int k = j % ns;
     const int step = len / (ns * R);
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      v[r] = x[j + r * span];
+      v[r] = x[line_pad(j + r * span)];
       if (r > 0 && k > 0) v[r] = cmul(v[r], tw[k * r * step]);
     }
     Dft<R, S>::run(v);
     const int base = (j / ns) * ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[base + r * ns] = v[r];
+    for (int r = 0; r < R; ++r) y[line_pad(base + r * ns)] = v[r];
   }
 }
 
-// One CTA per line; unnormalised DFT with exp(S 2 pi i n k / len).
-template <int S>
+// lines_per_cta lines per CTA; unnormalised DFT with exp(S 2 pi i n k / len).
+// Dynamic shared memory: lines_per_cta * 2 * line_padded_len(len) float2.
+template <int S, int LPC>
 __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
-  __shared__ float2 buf[2][kMaxFftLen];
-  const long long line = blockIdx.x;
-  float2 *base = f.data + (line / f.lines_per_batch) * f.batch_stride +
-                 (line % f.lines_per_batch) * f.line_stride;
-  for (int i = threadIdx.x; i < f.len; i += blockDim.x) buf[0][i] = base[(long long)i * f.elem_stride];
+  extern __shared__ float2 line_buf[];
+  constexpr int lpc = LPC;
+  const int len = f.len;
+  const long long line0 = (long long)blockIdx.x * lpc;
+  const long long off = (line0 / f.lines_per_batch) * f.batch_stride + (line0 % f.lines_per_batch) * f.line_stride;
+  const int l0 = (int)(line0 % f.lines_per_batch);
+  const int plen = line_padded_len(len);
+  float2 *base = f.data + off;
+  const float2 *in = (f.src ? f.src : f.data) + off;
+  // sample e of line c at e * elem_stride + c (adjacent lines: line_stride 1)
+  for (int i = threadIdx.x; i < len * lpc; i += blockDim.x) {
+    const int e = i / lpc, c = i - e * lpc;
+    line_buf[(size_t)c * 2 * plen + line_pad(e)] = in[(long long)e * f.elem_stride + c];
+  }
   __syncthreads();
+  // the CTA's threads form lpc groups, one per line; passes run in lockstep
+  const int nt = blockDim.x / lpc, grp = threadIdx.x / nt, t = threadIdx.x - grp * nt;
+  float2 *b0 = line_buf + (size_t)grp * 2 * plen;
   int cur = 0, ns = 1;
   for (int p = 0; p < f.nrad; ++p) {
     const int r = f.radix[p];
-    if (r == 4) stockham_pass<4, S>(buf[cur], buf[cur ^ 1], f.tw, f.len, ns);
-    else if (r == 2) stockham_pass<2, S>(buf[cur], buf[cur ^ 1], f.tw, f.len, ns);
-    else stockham_pass<3, S>(buf[cur], buf[cur ^ 1], f.tw, f.len, ns);
+    float2 *x = b0 + cur * plen, *y = b0 + (cur ^ 1) * plen;
+    if (r == 16) stockham_pass<16, S>(x, y, f.tw, len, ns, t, nt);
+    else if (r == 8) stockham_pass<8, S>(x, y, f.tw, len, ns, t, nt);
+    else if (r == 4) stockham_pass<4, S>(x, y, f.tw, len, ns, t, nt);
+    else if (r == 2) stockham_pass<2, S>(x, y, f.tw, len, ns, t, nt);
+    else stockham_pass<3, S>(x, y, f.tw, len, ns, t, nt);
     ns *= r;
     cur ^= 1;
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < f.len; i += blockDim.x) base[(long long)i * f.elem_stride] = buf[cur][i];
+  for (int i = threadIdx.x; i < len * lpc; i += blockDim.x) {
+    const int e = i / lpc, c = i - e * lpc;
+    float2 v = line_buf[(size_t)c * 2 * plen + cur * plen + line_pad(e)];
+    if (f.finish != 0.f) {
+      const float sc = ((e + l0 + c) & 1) ? -f.finish : f.finish;
+      v = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));
+    }
+    base[(long long)e * f.elem_stride + c] = v;
+  }
 }
 
 // sqrt of each tile's image of the first LED, as a complex m x m array per tile.

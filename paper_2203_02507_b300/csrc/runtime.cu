@@ -122,20 +122,18 @@ std::vector<float2> twiddles_line(int len, int sign) {
   return t;
 }
 
+// Radix plan of a line FFT: 16s first, then 8, 4, 2 and a 3 (lengths 2^a or 3 * 2^a).
 static bool radices_for(int len, FftLines &f) {
   int r = len, k = 0;
   if (r % 3 == 0) {
     f.radix[k++] = 3;
     r /= 3;
   }
-  while (r % 4 == 0 && k < kMaxRadices) {
-    f.radix[k++] = 4;
-    r /= 4;
-  }
-  if (r == 2 && k < kMaxRadices) {
-    f.radix[k++] = 2;
-    r = 1;
-  }
+  for (int rad : {16, 8, 4, 2})
+    while (r % rad == 0 && k < kMaxRadices) {
+      f.radix[k++] = rad;
+      r /= rad;
+    }
   f.nrad = k;
   return r == 1 && len <= kMaxFftLen;
 }
@@ -173,6 +171,8 @@ struct DeviceState {
   unsigned *err = nullptr;
   void *images = nullptr;                          // [T][L][m][m] column layout (tile_image_offset)
   size_t images_bytes = 0;
+  void *scratch = nullptr;                         // temporaries of the object / stitch calls
+  size_t scratch_bytes = 0;
   int32_t dtype = FPM_U16;
   float inv_counts = 1.f;
   bool loaded = false;
@@ -216,7 +216,7 @@ void destroy_device_state(fpm_plan *p) {
   }
   for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
                   (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
-                  d->images})
+                  d->images, d->scratch})
     dfree(q);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -281,31 +281,52 @@ static int ensure_device_state(fpm_plan *p) {
 }
 
 // Batched 1-D FFTs over lines of a device array.
-int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
-                     long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st) {
+int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int len, int sign, long long n_lines,
+                        int lines_per_batch, long long batch_stride, long long line_stride, long long elem_stride,
+                        float finish, cudaStream_t st) {
   FftLines f{};
   f.data = data;
+  f.src = src;
   f.tw = tw;
   f.len = len;
   f.batch_stride = batch_stride;
   f.line_stride = line_stride;
   f.elem_stride = elem_stride;
   f.lines_per_batch = lines_per_batch;
+  f.finish = finish;
+  // strided lines (columns): four adjacent ones per CTA, so loads and stores use whole sectors
+  f.lines_per_cta = (line_stride == 1 && elem_stride > 1 && lines_per_batch % 4 == 0 && n_lines % 4 == 0) ? 4 : 1;
   if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
-  const int threads = std::min(256, std::max(32, len / 4));
+  // one group of threads per line, a thread per radix-16 butterfly (whole warps)
+  const int group = std::min(256, std::max(32, (len / 16 + 31) / 32 * 32));
+  const int threads = group * f.lines_per_cta;
+  const size_t smem = (size_t)f.lines_per_cta * 2 * line_padded_len(len) * sizeof(float2);
+  void (*kern)(FftLines);
+  if (f.lines_per_cta == 4) kern = sign > 0 ? &fft_lines_kernel<1, 4> : &fft_lines_kernel<-1, 4>;
+  else kern = sign > 0 ? &fft_lines_kernel<1, 1> : &fft_lines_kernel<-1, 1>;
+  FPM_CK(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long max_chunk = (1LL << 30) / lines_per_batch * lines_per_batch;   // whole batches per launch
   for (long long done = 0; done < n_lines;) {
-    const long long chunk = std::min<long long>(n_lines - done, 1LL << 30);
+    const long long chunk = std::min<long long>(n_lines - done, max_chunk);
     FftLines g = f;
-    // offset the base so that line indices restart at a batch boundary
+    // offset the bases so that line indices restart at a batch boundary
     const long long first = done;
-    g.data = data + (first / lines_per_batch) * batch_stride + (first % lines_per_batch) * line_stride;
     if (first % lines_per_batch != 0) return fail(FPM_EINVAL, "internal: FFT chunk not batch aligned");
-    if (sign > 0) fft_lines_kernel<1><<<(unsigned)chunk, threads, 0, st>>>(g);
-    else fft_lines_kernel<-1><<<(unsigned)chunk, threads, 0, st>>>(g);
+    const long long off = (first / lines_per_batch) * batch_stride;
+    g.data = data + off;
+    g.src = src ? src + off : nullptr;
+    const unsigned ctas = (unsigned)(chunk / f.lines_per_cta);
+    kern<<<ctas, threads, smem, st>>>(g);
     done += chunk;
   }
   FPM_CK(cudaGetLastError());
   return FPM_OK;
+}
+
+int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
+                     long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st) {
+  return launch_fft_lines_ex(data, nullptr, tw, len, sign, n_lines, lines_per_batch, batch_stride, line_stride,
+                             elem_stride, 0.f, st);
 }
 
 static unsigned grid_for(long long n, int threads) {
@@ -439,6 +460,24 @@ int plan_image_dtype(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p-
 unsigned *plan_error_word(fpm_plan *p) { return p->dev ? p->dev->err : nullptr; }
 
 const float2 *plan_spectra(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->spec : nullptr; }
+
+int plan_scratch(fpm_plan *p, size_t bytes, void **out) {
+  DeviceState *d = p->dev;
+  *out = nullptr;
+  if (!d) return fail(FPM_ESTATE, "no device state before fpm_load_tiles");
+  if (d->scratch_bytes < bytes) {
+    if (d->scratch) cudaFree(d->scratch);          // synchronises: earlier users are done
+    d->scratch = nullptr;
+    d->scratch_bytes = 0;
+    if (cudaMalloc(&d->scratch, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FPM_ENOMEM, "device allocation of %zu bytes of scratch failed", bytes);
+    }
+    d->scratch_bytes = bytes;
+  }
+  *out = d->scratch;
+  return FPM_OK;
+}
 
 // Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
 // With `timed`, CUDA events bracket every update launch (waves mode only).

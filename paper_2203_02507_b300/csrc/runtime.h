@@ -10,6 +10,12 @@
 namespace fpm {
 // Twiddle table of the line FFT: exp(sign 2 pi i j / len), j < len.
 std::vector<float2> twiddles_line(int len, int sign);
+// Line FFTs out of place (src: input at the same offsets, null = in place), with
+// an optional finish: output sample e of line l (within its batch) times
+// finish * (-1)^(e + l).
+int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int len, int sign, long long n_lines,
+                        int lines_per_batch, long long batch_stride, long long line_stride, long long elem_stride,
+                        float finish, cudaStream_t st);
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
                      long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st);
 struct QueueJob;
@@ -45,6 +51,9 @@ int plan_image_dtype(const fpm_plan *p);
 unsigned *plan_error_word(fpm_plan *p);
 // The plan's spectra [T][N][N] (centred complex64) once loaded, else null.
 const float2 *plan_spectra(const fpm_plan *p);
+// A device scratch buffer of at least `bytes`, kept with the plan (grown on
+// demand, freed with the plan); its contents do not survive the next call.
+int plan_scratch(fpm_plan *p, size_t bytes, void **out);
 // Launch the pupil merge over `count` (tile, slots) entries.
 int launch_merge(float2 *pup, const float2 *dpup, const int2 *entries, int count, int y_lo, int rows, int m,
                  int slots, int disc, cudaStream_t st);
