@@ -288,6 +288,43 @@ def hbm_peak_gbs():
         return 6400.0, "fallback"
 
 
+def online_timing(plan, torch, host_stack, k, w):
+    """Online ingestion (Sec. 3.4): the FOV's images pushed one at a time from page-locked
+    host memory in the LED order, as fast as the host issues them.  Per image: device
+    time from its push to the end of the work it released (copy wait, gather, ready
+    wave steps); tail: the remaining loops after the last image."""
+    order = plan.schedule()["order"]
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in order]
+    end = torch.cuda.Event(enable_timing=True)
+    for warm in (True, False):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.online_begin(w.iters, dtype="u16", counts_per_unit=k)
+        before_last = 0
+        for i, led in enumerate(order):
+            if i == len(order) - 1:
+                before_last = plan.stats(check=False)["online_launched"]
+            ev[i][0].record(s)
+            plan.online_push(int(led), host_stack[int(led)])
+            ev[i][1].record(s)
+        plan.online_finish()
+        end.record(s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    per = sorted(a.elapsed_time(b) for a, b in ev[:-1])          # images before the last one
+    total_steps = plan.stats(check=False)["online_steps"]
+    return {"images": len(order), "per_image_ms_p50": per[len(per) // 2],
+            "per_image_ms_p99": per[int(0.99 * (len(per) - 1))], "per_image_ms_max": per[-1],
+            "last_image_to_done_ms": ev[-1][0].elapsed_time(end),
+            "device_ms_first_push_to_done": ev[0][0].elapsed_time(end), "wall_ms": wall * 1e3,
+            "steps_launched_before_last_image": before_last, "steps": total_steps,
+            "updates_per_s": w.updates / (ev[0][0].elapsed_time(end) / 1e3),
+            "how": "page-locked host images pushed in LED order without pacing; per image: device time of the "
+                   "work its push released (copy wait, gather, ready wave steps); the schedule is the offline "
+                   "one, so the result equals it bit for bit (tests/test_gpu_online.py)"}
+
+
 def stitch_timing(plan, torch, dev, stack, k, w, reps=3):
     """fpm_stitch of the reconstructed FOV into a device image (Eq. 1): device time and
     bandwidth on its algorithmic bytes (every spectrum read once, the image written once)."""
@@ -600,6 +637,7 @@ def main():
                                     "frac": fpu * u_l / t_l / 1e12 / peak,
                                     "share_of_step": s2["update_ms"] / pms}
         line[other + "_path"] = alt
+        line["online"] = online_timing(plan, torch, host_stack, k, w)
         del host_stack, host_out
         line["stitch"] = stitch_timing(plan, torch, dev, stack, k, w)
         line["uneven_batch"] = uneven_batch(torch, dev)

@@ -257,6 +257,8 @@ typedef struct {
   int32_t run_threads;      /* threads per CTA of the update kernel the last
                                fpm_reconstruct ran (a graph replay: the variant it was
                                captured with; persistent: the persistent kernel's)     */
+  int32_t online_launched;  /* wave steps the current or last online ingestion launched */
+  int32_t online_steps;     /* wave steps of its schedule                               */
   int32_t pad0;
 } fpm_stats;
 
@@ -379,6 +381,37 @@ FPM_API int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32
  * stream.  FPM_ECUDA on a CUDA failure.
  */
 FPM_API int fpm_fp32_peak(double *tflops, void *stream);
+
+/*
+ * Online reconstruction (Sec. 3.4, Fig. 7(a)): images are handed over one at a
+ * time while the sample is still being illuminated, and the updates that have
+ * all their images start at once, overlapping the acquisition.
+ *
+ * fpm_online_begin -- start ingesting `iters` (1..plan iters) loops' worth of
+ *   images of type dtype (FPM_U16 / FPM_F32) with intensity = element /
+ *   counts_per_unit.  Allocates the plan's device state and tile images as
+ *   fpm_load_tiles does, plus four staging images; the plan's previous state is
+ *   no longer readable until fpm_online_finish.
+ * fpm_online_push -- the sensor image taken with LED index `led`: sensor_h
+ *   rows of sensor_w elements, rows stride_row elements apart.  Host memory
+ *   (on_device 0) is copied on the plan's own copy stream; use page-locked
+ *   memory for the copy to overlap the running updates, and keep the buffer
+ *   unchanged until the work enqueued on `stream` by this call has completed.
+ *   Device memory is read stream-ordered on `stream`.  Its tile windows are
+ *   gathered, the initial guess is built when the order's first LED arrives,
+ *   and every wave step whose LEDs have all arrived is launched on `stream`.
+ *   Any order is accepted; in the LED order the first loop runs while the
+ *   images arrive.  FPM_EINVAL for an LED out of range or pushed twice.
+ * fpm_online_finish -- after all n_leds pushes: launch the remaining wave
+ *   steps; the plan then holds exactly the state fpm_load_tiles followed by
+ *   fpm_reconstruct(iters, FPM_RUN_WAVES) gives on the same images
+ *   (bit-identical).  FPM_ESTATE if images are missing.
+ * All three are stream-ordered; FPM_ESTATE when called out of sequence.
+ */
+FPM_API int fpm_online_begin(fpm_plan *plan, int32_t iters, int32_t dtype, float counts_per_unit, void *stream);
+FPM_API int fpm_online_push(fpm_plan *plan, int32_t led, const void *image, int32_t on_device, int64_t stride_row,
+                            void *stream);
+FPM_API int fpm_online_finish(fpm_plan *plan, void *stream);
 
 /*
  * fpm_get_object -- the tile's HR complex object o = IDFT_N(ifftshift(O)) with

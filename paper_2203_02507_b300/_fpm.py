@@ -69,7 +69,8 @@ class TuneEntry(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
                 ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
-                ("persistent_clusters", C.c_int32), ("run_threads", C.c_int32), ("pad0", C.c_int32)]
+                ("persistent_clusters", C.c_int32), ("run_threads", C.c_int32), ("online_launched", C.c_int32),
+                ("online_steps", C.c_int32), ("pad0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +100,9 @@ _SIGS = {
     "fpm_fp32_peak": [C.POINTER(C.c_double), _vp],
     "fpm_get_object": [_vp, _i32, _vp, _i32, _vp],
     "fpm_stitch": [_vp, _vp, _i32, _vp],
+    "fpm_online_begin": [_vp, _i32, _i32, _f32, _vp],
+    "fpm_online_push": [_vp, _i32, _vp, _i32, _i64, _vp],
+    "fpm_online_finish": [_vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -249,6 +253,31 @@ class Plan:
             out = np.zeros((self.m, self.m), np.complex64)
         _check(_lib.fpm_get_pupil(self._h, int(tile), _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
         return out
+
+    # -- online ingestion (images one at a time) ---------------------------
+    def online_begin(self, iters=None, dtype="u16", counts_per_unit=1.0, stream=None):
+        iters = self.iters if iters is None else iters
+        _check(_lib.fpm_online_begin(self._h, int(iters), U16 if dtype == "u16" else F32, float(counts_per_unit),
+                                     _stream(stream)))
+
+    def online_push(self, led: int, image, stream=None):
+        """image: [sensor_h, sensor_w] (rows may be strided) uint16/int16 or float32,
+        numpy (host) or torch (host or device)."""
+        if hasattr(image, "stride"):
+            stride_row = image.stride()[0] if callable(image.stride) else image.strides[0] // image.itemsize
+        else:
+            stride_row = image.strides[0] // image.itemsize
+        if hasattr(image, "data_ptr"):
+            ptr = image.data_ptr()
+        else:
+            if not image.flags.c_contiguous and image.strides[1] != image.itemsize:
+                raise ValueError("image rows must be contiguous")
+            ptr = image.ctypes.data
+        _check(_lib.fpm_online_push(self._h, int(led), ptr, 1 if _is_device(image) else 0, int(stride_row),
+                                    _stream(stream)))
+
+    def online_finish(self, stream=None):
+        _check(_lib.fpm_online_finish(self._h, _stream(stream)))
 
     def object(self, tile: int, out=None, stream=None):
         """The tile's HR complex object (fpm_get_object)."""

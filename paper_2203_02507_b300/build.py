@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-fvisibility=hidden",
           f"-I{os.path.join(ROOT, 'include')}"]
 CUFLAGS = ARCH + COMMON + ["-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
-SOURCES = ["plan.cpp", "runtime.cu", "persistent.cu", "server.cu", "noalloc.cu", "calib.cu", "stitch.cu"]
+SOURCES = ["plan.cpp", "runtime.cu", "persistent.cu", "server.cu", "noalloc.cu", "calib.cu", "stitch.cu", "online.cu"]
 HEADERS = ["internal.h", "runtime.h", "dft.cuh", "update.cuh", "aux_kernels.cuh", "update_args.h", "persistent.h", "tile_images.cuh"]
 
 

@@ -15,6 +15,7 @@ int fail(int code, const char *fmt, ...);
 void clear_error();
 
 struct DeviceState;   // device-side buffers of a plan (runtime.cu)
+struct OnlineState;   // image-by-image ingestion of a plan (online.cu)
 
 // Wave-step work lists of a plan's schedule, flattened for launches.  Step s
 // holds wave s of every tile that has one.
@@ -59,6 +60,7 @@ struct fpm_plan {
   int32_t cluster = 1, threads = 256;
 
   fpm::DeviceState *dev = nullptr;
+  fpm::OnlineState *online = nullptr;
   int32_t busy = 0;                 // > 0 while a server job owns the plan
 
   // cached step lists keyed by iteration count

@@ -144,7 +144,7 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
 
   // 0. the image in the update kernel's column layout
   fpm::tile_images_kernel<float><<<m / 32, 256, (size_t)m * 33 * sizeof(unsigned), st>>>(
-      d_img, image, (long long)m * m, m, d_sh + 1, m, fa, fb, 1, m / 32);
+      d_img, image, (long long)m * m, m, d_sh + 1, m, fa, fb, 1, 0, 1, m / 32);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(FPM_ECUDA, "image layout: %s", cudaGetErrorString(e));
 

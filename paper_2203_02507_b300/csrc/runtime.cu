@@ -200,6 +200,7 @@ static void dfree(void *p) {
 void forget_batches(fpm_plan *p);
 
 void destroy_device_state(fpm_plan *p) {
+  destroy_online_state(p);
   DeviceState *d = p->dev;
   if (!d) return;
   int cur = -1;
@@ -230,7 +231,7 @@ static int upload(T **dst, const void *src, size_t bytes) {
   return FPM_OK;
 }
 
-static int ensure_device_state(fpm_plan *p) {
+int ensure_device_state(fpm_plan *p) {
   if (p->dev) return FPM_OK;
   DeviceState *d = new DeviceState();
   p->dev = d;
@@ -334,13 +335,17 @@ static unsigned grid_for(long long n, int threads) {
 }
 
 // Initial guess of every tile from its image of the first LED in the order.
-static int run_init(fpm_plan *p, const void *stack, long long stride_led, long long stride_row, cudaStream_t st) {
+// `plane` is the sensor image of the first LED of the order (rows stride_row
+// elements apart).
+int run_init(fpm_plan *p, const void *plane, long long stride_row, cudaStream_t st) {
   DeviceState *d = p->dev;
   const int m = p->m, n = p->n, T = p->n_tiles;
   float2 *tmp = nullptr;
   FPM_CK(cudaMallocAsync((void **)&tmp, (size_t)T * m * m * sizeof(float2), st));
   const long long tot = (long long)T * m * m;
-  const int led = p->order[0];
+  const void *stack = plane;
+  const long long stride_led = 0;
+  const int led = 0;
   if (d->dtype == FPM_U16)
     init_gather_kernel<uint16_t><<<grid_for(tot, 256), 256, 0, st>>>(
         tmp, (const uint16_t *)stack, stride_led, stride_row, d->origins, led, m, T, d->inv_counts);
@@ -481,6 +486,30 @@ int plan_scratch(fpm_plan *p, size_t bytes, void **out) {
 
 // Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
 // With `timed`, CUDA events bracket every update launch (waves mode only).
+// Wave steps [s0, s1) of the `iters`-loop schedule, as FPM_RUN_WAVES runs them:
+// each step's update launch, then (EPRY) its pupil merge.
+int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t st) {
+  const StepLists &sl = step_lists(p, iters);
+  int rc = 0;
+  const StepDev *sd = device_steps(p, iters, sl, &rc);
+  if (!sd) return rc;
+  const UpdateArgs a = make_args(p, sd);
+  DeviceState *d = p->dev;
+  const int rows = p->y_hi - p->y_lo + 1;
+  for (int s = std::max(0, s0); s < std::min(s1, sl.n_steps); ++s) {
+    const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
+    if ((rc = launch_update(p, a, i0, i1 - i0, st))) return rc;
+    if (p->epry) {
+      const long long m0 = sl.merge_off[s], m1 = sl.merge_off[s + 1];
+      if ((rc = launch_merge(d->pup, d->dpup, sd->merges + m0, (int)(m1 - m0), p->y_lo, rows, p->m, p->max_width,
+                             p->disc_ok ? 1 : 0, st)))
+        return rc;
+    }
+  }
+  FPM_CK(cudaGetLastError());
+  return FPM_OK;
+}
+
 static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st, bool timed, bool capturing,
                                int64_t *launches) {
   const StepLists &sl = step_lists(p, iters);
@@ -718,6 +747,7 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
   out->run_launches = d->run_launches;
   out->persistent_clusters = d->persistent_clusters;
   out->run_threads = d->run_threads;
+  online_progress(p, &out->online_launched, &out->online_steps);
   const int derr = device_error(p);
   out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
   if (d->timed_valid && !d->timed_steps.empty()) {
@@ -768,13 +798,9 @@ int validate_stack(fpm_plan *p, const void *stack, int32_t dtype, int64_t stride
   return FPM_OK;
 }
 
-int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
-               int64_t stride_row, float counts_per_unit, cudaStream_t st) {
-  if (!stack) return fail(FPM_EINVAL, "fpm_load_tiles: null stack");
-  size_t bytes = 0;
-  int rc = validate_stack(p, stack, dtype, stride_led, stride_row, counts_per_unit, &bytes);
-  if (rc) return rc;
-  if ((rc = ensure_device_state(p))) return rc;
+// The tile-image buffer for images of type dtype (reallocated, with the launch
+// caches that hold its address, when the size changes).
+int ensure_images(fpm_plan *p, int32_t dtype) {
   DeviceState *d = p->dev;
   const size_t ib = image_bytes(p, dtype);
   if (d->images_bytes != ib) {
@@ -796,6 +822,49 @@ int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device,
     }
     d->images_bytes = ib;
   }
+  return FPM_OK;
+}
+
+// Gather n_src sensor images (LEDs led0 ..) into the tile-image buffer.
+int gather_tile_images(fpm_plan *p, const void *src, int32_t dtype, long long stride_led, long long stride_row,
+                       int led0, int n_src, cudaStream_t st) {
+  DeviceState *d = p->dev;
+  const int m = p->m;
+  const long long n_blocks = (long long)p->n_tiles * n_src * (m / 32);
+  const unsigned grid = (unsigned)std::min<long long>(n_blocks, 148LL * 16);
+  const size_t smem = (size_t)m * 33 * sizeof(unsigned);
+  if (dtype == FPM_U16)
+    tile_images_kernel<uint16_t><<<grid, 256, smem, st>>>((uint16_t *)d->images, (const uint16_t *)src, stride_led,
+                                                          stride_row, d->origins, m, d->var->a, d->var->b, p->n_leds,
+                                                          led0, n_src, n_blocks);
+  else
+    tile_images_kernel<float><<<grid, 256, smem, st>>>((float *)d->images, (const float *)src, stride_led, stride_row,
+                                                       d->origins, m, d->var->a, d->var->b, p->n_leds, led0, n_src,
+                                                       n_blocks);
+  FPM_CK(cudaGetLastError());
+  return FPM_OK;
+}
+
+int begin_load(fpm_plan *p, int32_t dtype, float counts_per_unit, cudaStream_t st) {
+  DeviceState *d = p->dev;
+  d->loaded = false;
+  d->dtype = dtype;
+  d->inv_counts = 1.0f / counts_per_unit;
+  FPM_CK(cudaMemsetAsync(d->err, 0, 4 * sizeof(unsigned), st));   // a reload clears a previous failure
+  return FPM_OK;
+}
+
+void mark_loaded(fpm_plan *p) { p->dev->loaded = true; }
+
+int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device, int64_t stride_led,
+               int64_t stride_row, float counts_per_unit, cudaStream_t st) {
+  if (!stack) return fail(FPM_EINVAL, "fpm_load_tiles: null stack");
+  size_t bytes = 0;
+  int rc = validate_stack(p, stack, dtype, stride_led, stride_row, counts_per_unit, &bytes);
+  if (rc) return rc;
+  if ((rc = ensure_device_state(p))) return rc;
+  DeviceState *d = p->dev;
+  if ((rc = ensure_images(p, dtype))) return rc;
   const void *src = stack;
   void *staging = nullptr;        // a host stack passes through device memory once, for the gather
   if (on_device) {
@@ -813,23 +882,13 @@ int load_tiles(fpm_plan *p, const void *stack, int32_t dtype, int32_t on_device,
     FPM_CK(cudaMemcpyAsync(staging, stack, bytes, cudaMemcpyHostToDevice, st));
     src = staging;
   }
-  d->dtype = dtype;
-  d->inv_counts = 1.0f / counts_per_unit;
-  FPM_CK(cudaMemsetAsync(d->err, 0, 4 * sizeof(unsigned), st));   // a reload clears a previous failure
-  // every tile's images in the update kernel's column layout
-  const int m = p->m;
-  const long long n_blocks = (long long)p->n_tiles * p->n_leds * (m / 32);
-  const unsigned grid = (unsigned)std::min<long long>(n_blocks, 148LL * 16);
-  const size_t smem = (size_t)m * 33 * sizeof(unsigned);
-  if (dtype == FPM_U16)
-    tile_images_kernel<uint16_t><<<grid, 256, smem, st>>>((uint16_t *)d->images, (const uint16_t *)src, stride_led,
-                                                          stride_row, d->origins, m, d->var->a, d->var->b, p->n_leds,
-                                                          n_blocks);
-  else
-    tile_images_kernel<float><<<grid, 256, smem, st>>>((float *)d->images, (const float *)src, stride_led, stride_row,
-                                                       d->origins, m, d->var->a, d->var->b, p->n_leds, n_blocks);
-  FPM_CK(cudaGetLastError());
-  rc = run_init(p, src, stride_led, stride_row, st);
+  if ((rc = begin_load(p, dtype, counts_per_unit, st))) return rc;
+  // every tile's images in the update kernel's column layout, then the initial guess
+  rc = gather_tile_images(p, src, dtype, stride_led, stride_row, 0, p->n_leds, st);
+  if (!rc) {
+    const size_t es = dtype == FPM_U16 ? 2 : 4;
+    rc = run_init(p, static_cast<const char *>(src) + (size_t)p->order[0] * stride_led * es, stride_row, st);
+  }
   if (staging) cudaFreeAsync(staging, st);
   if (rc) return rc;
   d->loaded = true;

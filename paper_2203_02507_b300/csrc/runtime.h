@@ -32,6 +32,27 @@ void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd);
 // Launch the update kernel over items [item0, item0 + count) (image dtype FPM_U16 or FPM_F32).
 int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
                         cudaStream_t st);
+// The plan's device state (tables, spectra, pupils), created on first use.
+int ensure_device_state(fpm_plan *p);
+// Free the plan's online-ingestion state, if any (online.cu).
+void destroy_online_state(fpm_plan *p);
+// Wave steps launched so far by the plan's online ingestion, and in its schedule (0, 0 if none).
+void online_progress(const fpm_plan *p, int32_t *launched, int32_t *total);
+// The tile-image buffer for images of type dtype, (re)allocated as needed.
+int ensure_images(fpm_plan *p, int32_t dtype);
+// Gather n_src sensor images (LEDs led0 .. led0 + n_src - 1, planes stride_led
+// elements apart) into the tile-image buffer, stream-ordered.
+int gather_tile_images(fpm_plan *p, const void *src, int32_t dtype, long long stride_led, long long stride_row,
+                       int led0, int n_src, cudaStream_t st);
+// Initial guess of every tile from `plane`, the sensor image of the order's first
+// LED (rows stride_row elements apart); resets the pupils.  Uses the plan's dtype.
+int run_init(fpm_plan *p, const void *plane, long long stride_row, cudaStream_t st);
+// Wave steps [s0, s1) of the `iters`-loop schedule, launched as FPM_RUN_WAVES does.
+int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t st);
+// Set the plan's image type and intensity scale and clear its error word (before a load).
+int begin_load(fpm_plan *p, int32_t dtype, float counts_per_unit, cudaStream_t st);
+// Mark the plan loaded (its state is ready for fpm_reconstruct and the getters).
+void mark_loaded(fpm_plan *p);
 // Validate an image stack description; *bytes (if set) = its extent in bytes.
 int validate_stack(fpm_plan *p, const void *stack, int32_t dtype, int64_t stride_led, int64_t stride_row,
                    float counts_per_unit, size_t *bytes);

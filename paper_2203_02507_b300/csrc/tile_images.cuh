@@ -7,19 +7,21 @@
 namespace fpm {
 
 // Tile images in the update kernel's column layout (tile_image_offset):
-// out[t][l][x][k1 * b + k2] = stack[l][y0_t + k1 + a k2][x0_t + x].  One block
-// per (tile, LED, 32 columns): the block reads the 32 columns row by row into
-// shared memory (pitch 33 words) and writes them out column by column.
+// out[t][led0 + l][x][k1 * b + k2] = stack[l][y0_t + k1 + a k2][x0_t + x] for
+// the n_src images l of `stack` (LEDs led0 .. led0 + n_src - 1 of n_leds).  One
+// block per (tile, image, 32 columns): the block reads the 32 columns row by
+// row into shared memory (pitch 33 words) and writes them out column by column.
 // Shared memory: m * 33 * 4 bytes.
 template <typename Img>
 __global__ void tile_images_kernel(Img *out, const Img *stack, long long stride_led, long long stride_row,
-                                   const int2 *origins, int m, int a, int b, int n_leds, long long n_blocks) {
+                                   const int2 *origins, int m, int a, int b, int n_leds, int led0, int n_src,
+                                   long long n_blocks) {
   extern __shared__ unsigned col_buf[];
   const int chunks = m / 32;
   for (long long blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const int chunk = (int)(blk % chunks);
-    const int l = (int)((blk / chunks) % n_leds);
-    const int t = (int)(blk / ((long long)chunks * n_leds));
+    const int l = (int)((blk / chunks) % n_src);
+    const int t = (int)(blk / ((long long)chunks * n_src));
     const int x0 = chunk * 32;
     const int2 o = origins[t];
     const Img *src = stack + (long long)l * stride_led + (long long)o.x * stride_row + o.y + x0;
@@ -31,7 +33,7 @@ __global__ void tile_images_kernel(Img *out, const Img *stack, long long stride_
       else col_buf[y * 33 + x] = __float_as_uint(v);
     }
     __syncthreads();
-    Img *dst = out + tile_image_offset(t, l, n_leds, m) + (size_t)x0 * m;
+    Img *dst = out + tile_image_offset(t, led0 + l, n_leds, m) + (size_t)x0 * m;
     for (int i = threadIdx.x; i < m * 32; i += blockDim.x) {
       const int x = i / m, j = i - x * m;
       const int y = j / b + a * (j % b);
