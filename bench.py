@@ -288,6 +288,30 @@ def hbm_peak_gbs():
         return 6400.0, "fallback"
 
 
+def sequential_timing(torch, stack, k, w, steps=2):
+    """Strict-sequential EPRY (FPM_SEQUENTIAL: one LED per tile per wave) on the same FOV,
+    the whole job per step as in the headline, both execution paths."""
+    from paper_2203_02507_b300 import plan_for
+    p = plan_for(w, sequential=True)
+    s = torch.cuda.current_stream()
+    out = {"waves_per_tile": p.info["max_waves"], "updates_per_step": w.updates}
+    for mode in ("waves", "persistent"):
+        p.load_tiles(stack, k)
+        p.reconstruct(w.iters, mode=mode, graph=True)          # warm-up (graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            p.load_tiles(stack, k)
+            p.reconstruct(w.iters, mode=mode, graph=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[mode] = {"updates_per_s": w.updates / (ms / 1e3), "ms_per_step": ms}
+    p.close()
+    return out
+
+
 def online_timing(plan, torch, host_stack, k, w):
     """Online ingestion (Sec. 3.4): the FOV's images pushed one at a time from page-locked
     host memory in the LED order, as fast as the host issues them.  Per image: device
@@ -639,6 +663,7 @@ def main():
         line[other + "_path"] = alt
         line["online"] = online_timing(plan, torch, host_stack, k, w)
         del host_stack, host_out
+        line["sequential_epry"] = sequential_timing(torch, stack, k, w)
         line["stitch"] = stitch_timing(plan, torch, dev, stack, k, w)
         line["uneven_batch"] = uneven_batch(torch, dev)
         if args.serving_jobs > 0:

@@ -64,6 +64,10 @@ extern "C" {
 
 /* ---- plan flags ------------------------------------------------------------ */
 #define FPM_EPRY  1u  /* correct the pupil too (embedded pupil recovery)          */
+#define FPM_SEQUENTIAL 2u /* strict sequential order: every update sees the pupil
+                             corrected by all earlier ones (each wave holds one LED
+                             per tile); default: wave-synchronous, LEDs whose
+                             sub-apertures share no spectrum pixel in one wave   */
 
 /* ---- image element types --------------------------------------------------- */
 #define FPM_U16 0     /* camera counts (e.g. 12-bit)                             */
@@ -108,7 +112,7 @@ typedef struct {
   const double *defocus_um;     /* [tiles_y * tiles_x] per-tile defocus, or NULL = 0   */
   int32_t order;                /* FPM_ORDER_*                                         */
   int32_t iters;                /* iteration loops the schedule is built for (>= 1)    */
-  uint32_t flags;               /* FPM_EPRY or 0                                        */
+  uint32_t flags;               /* FPM_EPRY | FPM_SEQUENTIAL, or 0                      */
 } fpm_plan_desc;
 
 /* Sizes of a plan, for allocating the arrays the getters fill. */

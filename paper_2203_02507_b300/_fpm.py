@@ -20,6 +20,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EBUSY, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ORDER = {"center_out": 0, "raster": 1}
 EPRY = 1
+SEQUENTIAL = 2
 U16, F32 = 0, 1
 RUN = {"plain": 0, "waves": 1, "persistent": 2, "auto": 3}
 RUN_GRAPH = 0x100
@@ -158,7 +159,8 @@ class Plan:
     """An FPM job: geometry, schedule, and (after load_tiles) device state."""
 
     def __init__(self, *, sensor, tile, overlap, tiles, upsample, wavelength_um, na, pixel_um,
-                 led_xy_um, led_height_um, defocus_um=None, order="center_out", iters=1, epry=False):
+                 led_xy_um, led_height_um, defocus_um=None, order="center_out", iters=1, epry=False,
+                 sequential=False):
         sh, sw = (sensor, sensor) if np.isscalar(sensor) else sensor
         ty, tx = (tiles, tiles) if np.isscalar(tiles) else tiles
         self._leds = np.ascontiguousarray(led_xy_um, dtype=np.float64).reshape(-1, 2)
@@ -175,7 +177,7 @@ class Plan:
                         if self._defocus is not None else None)
         d.order = ORDER[order]
         d.iters = int(iters)
-        d.flags = EPRY if epry else 0
+        d.flags = (EPRY if epry else 0) | (SEQUENTIAL if sequential else 0)
         h = _vp()
         _check(_lib.fpm_plan_create(C.byref(d), C.byref(h)))
         self._h = h
@@ -382,7 +384,7 @@ def fp32_peak(stream=None) -> float:
     return v.value
 
 
-def plan_for(workload, defocus_um=None, iters=None) -> Plan:
+def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="center_out") -> Plan:
     """Plan of a synth.Workload (square sensor and grid)."""
     from synth import led_grid, tile_defocus
     o = workload.optics
@@ -392,4 +394,5 @@ def plan_for(workload, defocus_um=None, iters=None) -> Plan:
     return Plan(sensor=workload.sensor, tile=workload.tile, overlap=workload.overlap, tiles=workload.tiles,
                 upsample=workload.upsample, wavelength_um=o.wavelength_um, na=o.na, pixel_um=o.pixel_um,
                 led_xy_um=led_grid(o.led_side, o.led_pitch_um), led_height_um=o.led_height_um,
-                defocus_um=defocus_um, iters=iters or workload.iters, epry=workload.epry)
+                defocus_um=defocus_um, iters=iters or workload.iters, epry=workload.epry, sequential=sequential,
+                order=order)

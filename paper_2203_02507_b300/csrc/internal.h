@@ -39,6 +39,7 @@ struct fpm_plan {
   int32_t upsample = 0, n = 0, n_tiles = 0, n_leds = 0, iters = 0, order_kind = 0;
   double wavelength_um = 0, na = 0, pixel_um = 0, led_height_um = 0, df = 0;
   bool epry = false;
+  bool sequential = false;          // FPM_SEQUENTIAL: one update per wave
   std::vector<double> led_xy, defocus;
 
   // data-independent quantities (host, FP64 -> int / complex64)

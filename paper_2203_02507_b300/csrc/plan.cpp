@@ -221,7 +221,11 @@ static void build_waves(fpm_plan *p) {
     for (int j = 0; j < S; ++j) {
       const int l = p->order[j % L];
       int32_t mx = -1;
-      for (int b : nbr[l]) mx = std::max(mx, last[b]);
+      if (p->sequential) {
+        mx = j - 1;                      // strict sequence: one update per wave
+      } else {
+        for (int b : nbr[l]) mx = std::max(mx, last[b]);
+      }
       w[j] = mx + 1;
       last[l] = mx + 1;
       top = std::max(top, mx + 1);
@@ -327,7 +331,7 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
   if (d->iters < 1 || d->iters > 10000) return fail(FPM_EINVAL, "iters %d out of range", d->iters);
   if (d->order != FPM_ORDER_CENTER_OUT && d->order != FPM_ORDER_RASTER)
     return fail(FPM_EINVAL, "unknown order %d", d->order);
-  if (d->flags & ~FPM_EPRY) return fail(FPM_EINVAL, "unknown flags 0x%x", d->flags);
+  if (d->flags & ~(FPM_EPRY | FPM_SEQUENTIAL)) return fail(FPM_EINVAL, "unknown flags 0x%x", d->flags);
 
   fpm_plan *p = new (std::nothrow) fpm_plan();
   if (!p) return fail(FPM_ENOMEM, "out of host memory");
@@ -348,6 +352,7 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
   p->pixel_um = d->pixel_um;
   p->led_height_um = d->led_height_um;
   p->epry = (d->flags & FPM_EPRY) != 0;
+  p->sequential = (d->flags & FPM_SEQUENTIAL) != 0;
   p->df = 1.0 / (m * d->pixel_um);
   p->led_xy.assign(d->led_xy_um, d->led_xy_um + (size_t)d->n_leds * 2);
   for (double v : p->led_xy)

@@ -33,10 +33,11 @@ def _update32(spectrum, pupil_, support, shift, intensity, p_norm):
     return np.where(support, np.conj(old) * delta / o_norm, 0).astype(np.complex64)
 
 
-def reconstruct_tile32(images, shifts, order, support, pupil0, n, iters, epry):
-    """Wave-synchronous reconstruction of one tile in complex64 (see fpm_oracle.reconstruct_tile)."""
+def reconstruct_tile32(images, shifts, order, support, pupil0, n, iters, epry, mode="waves"):
+    """Reconstruction of one tile in complex64 (see fpm_oracle.reconstruct_tile): wave-
+    synchronous, or strict sequential (one update per wave)."""
     seq = orc.sequence(order, iters)
-    w = orc.waves(n, support, shifts, seq)
+    w = orc.waves(n, support, shifts, seq) if mode == "waves" else np.arange(len(seq))
     spec = orc.initial_spectrum(images[int(order[0])], n).astype(np.complex64)
     p = pupil0.astype(np.complex64)
     for wid in range(int(w.max()) + 1):
@@ -51,9 +52,9 @@ def reconstruct_tile32(images, shifts, order, support, pupil0, n, iters, epry):
     return spec, p
 
 
-def floor(images, shifts, order, support, pupil0, n, iters, epry, ref_spec, ref_pup):
+def floor(images, shifts, order, support, pupil0, n, iters, epry, ref_spec, ref_pup, mode="waves"):
     """(spectrum, pupil) rel-L2 of the complex64 run against the FP64 oracle's result."""
-    s32, p32 = reconstruct_tile32(images, shifts, order, support, pupil0, n, iters, epry)
+    s32, p32 = reconstruct_tile32(images, shifts, order, support, pupil0, n, iters, epry, mode)
     rs = float(np.linalg.norm(s32 - ref_spec) / np.linalg.norm(ref_spec))
     rp = float(np.linalg.norm(p32 - ref_pup) / np.linalg.norm(ref_pup))
     return rs, rp

@@ -94,3 +94,13 @@ def test_device_calls_before_load_fail_cleanly():
     with pytest.raises(fpm.FpmError):
         p.spectrum(0)
     p.close()
+
+
+def test_sequential_flag_gives_one_update_per_wave():
+    w = synth.WORKLOADS["tile64_plain"]
+    p = fpm.plan_for(w, iters=2, sequential=True)
+    s = p.schedule()
+    for t in range(w.n_tiles):
+        assert list(s["waves"][t]) == list(range(2 * w.n_leds))
+    assert p.info["max_wave_width"] == 1 and p.info["max_waves"] == 2 * w.n_leds
+    p.close()

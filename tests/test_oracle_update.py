@@ -101,3 +101,31 @@ def test_reconstruction_error_decreases():
         ph /= abs(ph)
         errs.append(np.linalg.norm(o[band] * ph - spec[band]) / np.linalg.norm(spec[band]))
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_sequential_epry_equals_waves_when_every_wave_has_one_led():
+    """All LEDs on one footprint: every wave holds a single LED, so wave-synchronous
+    EPRY takes exactly the strict-sequential steps (a pin of the sequential mode
+    through the independently pinned wave mode)."""
+    g, spec, imgs = _small_job(z=3.0, seed=5)
+    same = np.zeros_like(g.shifts[0])                      # every LED on the centre footprint
+    init = orc.initial_spectrum(imgs[int(g.order[0])], g.n)
+    w = orc.waves(g.n, g.support, same, orc.sequence(g.order, 2))
+    assert list(w) == list(range(len(w)))
+    a = orc.reconstruct_tile(imgs, same, g.order, g.support, g.pupils[0], g.n, 2, True, mode="waves",
+                             spectrum0=init)
+    b = orc.reconstruct_tile(imgs, same, g.order, g.support, g.pupils[0], g.n, 2, True, mode="sequential",
+                             spectrum0=init)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_sequential_epry_differs_from_waves_when_leds_share_a_wave():
+    """With disjoint footprints in a wave, sequential EPRY lets each later LED see the
+    earlier corrections: the two modes then give different pupils."""
+    g, spec, imgs = _small_job(z=3.0, seed=5)
+    init = orc.initial_spectrum(imgs[int(g.order[0])], g.n)
+    a = orc.reconstruct_tile(imgs, g.shifts[0], g.order, g.support, g.pupils[0], g.n, 1, True, mode="waves",
+                             spectrum0=init)
+    b = orc.reconstruct_tile(imgs, g.shifts[0], g.order, g.support, g.pupils[0], g.n, 1, True,
+                             mode="sequential", spectrum0=init)
+    assert not np.array_equal(a[1], b[1])
