@@ -493,6 +493,8 @@ def main():
                     help="auto: fpm_autotune picks the fastest path on one loop of the data")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
     ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
+    ap.add_argument("--only", choices=["stitch", "online", "sequential"],
+                    help="time only this part on the workload (profiling aid) and print its JSON")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -513,6 +515,17 @@ def main():
     plan = plan_for(w)
     stack, k = device_stack(plan, w, torch, dev)
     stream = torch.cuda.current_stream()
+    if args.only:
+        if args.only == "stitch":
+            part = stitch_timing(plan, torch, dev, stack, k, w)
+        elif args.only == "sequential":
+            part = sequential_timing(torch, stack, k, w)
+        else:
+            host_stack = torch.empty(stack.shape, dtype=stack.dtype, pin_memory=True)
+            host_stack.copy_(stack)
+            part = online_timing(plan, torch, host_stack, k, w)
+        print(json.dumps({"part": args.only, "workload": w.name, args.only: part}))
+        return
     tune = None
     if args.mode == "auto":
         plan.load_tiles(stack, k)
