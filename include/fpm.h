@@ -237,6 +237,17 @@ FPM_API int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, 
  * after the copy completed.
  */
 FPM_API int fpm_get_spectrum(fpm_plan *plan, int32_t tile, void *dst, int32_t on_device, void *stream);
+
+/*
+ * fpm_get_spectra -- every tile's spectrum, [n_tiles][N][N] centred complex64,
+ * copied to `dst` (host memory if on_device == 0, device memory otherwise) by
+ * one copy enqueued on `stream`; the call does not wait for it, so with
+ * page-locked host memory the copy overlaps other work and the caller
+ * synchronises the stream before reading.  A bounded device wait that gave up
+ * in the last persistent run is reported by fpm_get_stats.  FPM_ESTATE before
+ * fpm_load_tiles.
+ */
+FPM_API int fpm_get_spectra(fpm_plan *plan, void *dst, int32_t on_device, void *stream);
 FPM_API int fpm_get_pupil(fpm_plan *plan, int32_t tile, void *dst, int32_t on_device, void *stream);
 
 /*
@@ -276,13 +287,16 @@ typedef struct {
   int32_t mode;      /* FPM_RUN_WAVES or FPM_RUN_PERSISTENT                      */
   int32_t threads;   /* threads per CTA of the update kernel                     */
   int32_t cluster;   /* CTAs per update                                          */
+  int32_t branches;  /* wave launches: parallel graph branches over tile groups  */
   double ms;         /* device time of `iters` loops on the plan's data          */
 } fpm_tune_entry;
 
 /*
  * fpm_autotune -- time every execution path that fits the plan's tile side
  * (wave-by-wave launches with each update-kernel variant -- threads per CTA,
- * CTAs per SM -- and the persistent kernel) on `iters` loops of the plan's own
+ * CTAs per SM -- and, for the first variant, with the tiles split into 2, 4
+ * and 8 groups whose wave steps run as parallel graph branches; and the persistent
+ * kernel) on `iters` loops of the plan's own
  * loaded data, each replayed as a CUDA graph after a warm-up, and keep the
  * fastest for FPM_RUN_AUTO and for FPM_RUN_WAVES.  The plan's spectra and pupils
  * are saved first and restored afterwards.  entries (may be NULL) receives up

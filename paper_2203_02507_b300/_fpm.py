@@ -64,7 +64,8 @@ class PlanInfo(C.Structure):
 
 
 class TuneEntry(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("threads", C.c_int32), ("cluster", C.c_int32), ("ms", C.c_double)]
+    _fields_ = [("mode", C.c_int32), ("threads", C.c_int32), ("cluster", C.c_int32), ("branches", C.c_int32),
+                ("ms", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -104,6 +105,7 @@ _SIGS = {
     "fpm_online_begin": [_vp, _i32, _i32, _f32, _vp],
     "fpm_online_push": [_vp, _i32, _vp, _i32, _i64, _vp],
     "fpm_online_finish": [_vp, _vp],
+    "fpm_get_spectra": [_vp, _vp, _i32, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -234,7 +236,8 @@ class Plan:
         n, best = _i32(), _i32()
         _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, 16, C.byref(n), C.byref(best)))
         names = {v: k for k, v in RUN.items()}
-        out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "ms": e.ms} for e in ent[:n.value]]
+        out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "branches": e.branches, "ms": e.ms}
+               for e in ent[:n.value]]
         return out, best.value
 
     def stats(self, check: bool = True) -> dict:
@@ -248,6 +251,12 @@ class Plan:
         if out is None:
             out = np.zeros((self.n, self.n), np.complex64)
         _check(_lib.fpm_get_spectrum(self._h, int(tile), _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
+        return out
+
+    def spectra(self, out, stream=None):
+        """All tiles' spectra into `out` ([T, N, N] complex64, host or device), one copy
+        enqueued on the stream and not waited for (fpm_get_spectra)."""
+        _check(_lib.fpm_get_spectra(self._h, _ptr(out), 1 if _is_device(out) else 0, _stream(stream)))
         return out
 
     def pupil(self, tile: int, out=None, stream=None):

@@ -161,6 +161,8 @@ struct GraphKey {
   }
 };
 
+constexpr int kMaxBranches = 8;
+
 struct DeviceState {
   int device = -1;
   float2 *spec = nullptr, *pup = nullptr, *dpup = nullptr;   // pup: [T][m][m]; dpup: [T][W][m][m]
@@ -191,6 +193,11 @@ struct DeviceState {
   std::map<int32_t, QueueDev *> queues;        // persistent queues by loop count
   int persistent_clusters = 0;
   int tuned_mode = FPM_RUN_PERSISTENT;         // FPM_RUN_AUTO resolves to this
+  // graph replays of FPM_RUN_WAVES split the tiles into `branches` groups whose
+  // wave steps run as parallel branches of the graph (tiles are independent)
+  int32_t branches = 1;
+  cudaStream_t branch_st[kMaxBranches] = {};
+  cudaEvent_t branch_ev[2 * kMaxBranches] = {};
 };
 
 static void dfree(void *p) {
@@ -209,6 +216,10 @@ void destroy_device_state(fpm_plan *p) {
   cudaDeviceSynchronize();
   for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);
   for (cudaEvent_t ev : d->events) cudaEventDestroy(ev);
+  for (cudaStream_t bs : d->branch_st)
+    if (bs) cudaStreamDestroy(bs);
+  for (cudaEvent_t ev : d->branch_ev)
+    if (ev) cudaEventDestroy(ev);
   for (auto &kv : d->queues) free_queue(kv.second);
   forget_batches(p);
   for (auto &s : d->steps) {
@@ -239,6 +250,7 @@ int ensure_device_state(fpm_plan *p) {
   const int rows = p->y_hi - p->y_lo + 1;
   d->var = find_variant(p->m, rows);
   if (!d->var) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", p->m, rows);
+  if (const char *env = getenv("FPM_WAVE_BRANCHES")) d->branches = std::max(1, std::min(kMaxBranches, atoi(env)));
   const size_t T = p->n_tiles, n = p->n, m = p->m;
   cudaError_t e;
   for (const auto &v : variants())            // every fitting variant may be chosen by the autotuner
@@ -508,6 +520,77 @@ int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t 
   }
   FPM_CK(cudaGetLastError());
   return FPM_OK;
+}
+
+// All wave steps of the `iters`-loop schedule restricted to tiles [t0, t1) (a
+// step's items and merges are sorted by tile, so the range is contiguous).
+static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int t0, int t1, cudaStream_t st, int64_t *launches) {
+  const StepLists &sl = step_lists(p, iters);
+  int rc = 0;
+  const StepDev *sd = device_steps(p, iters, sl, &rc);
+  if (!sd) return rc;
+  const UpdateArgs a = make_args(p, sd);
+  DeviceState *d = p->dev;
+  const int rows = p->y_hi - p->y_lo + 1;
+  const int32_t *items = sl.items.data(), *merges = sl.merges.data();
+  auto first_item = [&](int64_t lo, int64_t hi, int t) {       // first item of tile >= t in [lo, hi)
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (items[mid * 4] < t) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  auto first_merge = [&](int64_t lo, int64_t hi, int t) {
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (merges[mid * 2] < t) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  int64_t nl = 0;
+  for (int s = 0; s < sl.n_steps; ++s) {
+    const int64_t i0 = first_item(sl.step_off[s], sl.step_off[s + 1], t0);
+    const int64_t i1 = first_item(i0, sl.step_off[s + 1], t1);
+    if (i1 == i0) continue;
+    if ((rc = launch_update(p, a, i0, i1 - i0, st))) return rc;
+    ++nl;
+    if (p->epry) {
+      const int64_t m0 = first_merge(sl.merge_off[s], sl.merge_off[s + 1], t0);
+      const int64_t m1 = first_merge(m0, sl.merge_off[s + 1], t1);
+      if ((rc = launch_merge(d->pup, d->dpup, sd->merges + m0, (int)(m1 - m0), p->y_lo, rows, p->m, p->max_width,
+                             p->disc_ok ? 1 : 0, st)))
+        return rc;
+      if (m1 > m0) ++nl;
+    }
+  }
+  FPM_CK(cudaGetLastError());
+  *launches += nl;
+  return FPM_OK;
+}
+
+// The wave steps as `branches` parallel branches over tile groups: forked from
+// and joined back into the (capturing) stream st with events.
+static int enqueue_wave_branches(fpm_plan *p, int32_t iters, int branches, cudaStream_t st, int64_t *launches) {
+  DeviceState *d = p->dev;
+  for (int k = 0; k < branches; ++k) {
+    if (k > 0 && !d->branch_st[k]) FPM_CK(cudaStreamCreateWithFlags(&d->branch_st[k], cudaStreamNonBlocking));
+    for (int e = 0; e < 2; ++e)
+      if (!d->branch_ev[2 * k + e]) FPM_CK(cudaEventCreateWithFlags(&d->branch_ev[2 * k + e], cudaEventDisableTiming));
+  }
+  FPM_CK(cudaEventRecord(d->branch_ev[0], st));                 // fork
+  for (int k = 1; k < branches; ++k) FPM_CK(cudaStreamWaitEvent(d->branch_st[k], d->branch_ev[0], 0));
+  int rc = FPM_OK;
+  for (int k = 0; k < branches && rc == FPM_OK; ++k) {
+    const int t0 = (int)((int64_t)p->n_tiles * k / branches), t1 = (int)((int64_t)p->n_tiles * (k + 1) / branches);
+    rc = enqueue_wave_tiles(p, iters, t0, t1, k == 0 ? st : d->branch_st[k], launches);
+  }
+  for (int k = 1; k < branches; ++k) {                          // join (also after a failure, to end the capture cleanly)
+    FPM_CK(cudaEventRecord(d->branch_ev[2 * k + 1], d->branch_st[k]));
+    FPM_CK(cudaStreamWaitEvent(st, d->branch_ev[2 * k + 1], 0));
+  }
+  return rc;
 }
 
 static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_t st, bool timed, bool capturing,
@@ -940,7 +1023,8 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     d->run_threads = d->var->t;
     return rc;
   }
-  fpm::GraphKey key{iters, mode & 0xfff, st};
+  const int branches = (base == FPM_RUN_WAVES && !timed) ? std::min(d->branches, std::max(1, p->n_tiles)) : 1;
+  fpm::GraphKey key{iters, (mode & 0xfff) | (branches << 12), st};
   auto it = d->graphs.find(key);
   if (it == d->graphs.end()) {
     // build step lists and device copies outside the capture
@@ -955,7 +1039,8 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     }
     FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     int64_t nl = 0;
-    rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
+    if (branches > 1) rc = fpm::enqueue_wave_branches(p, iters, branches, cap, &nl);
+    else rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
     d->graph_launches[key] = nl;
     d->graph_threads[key] = d->var->t;
     cudaGraph_t g = nullptr;
@@ -1026,13 +1111,21 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
   struct Cand {
     int mode;
     const fpm::Variant *v;
+    int branches;
     double ms;
   };
   std::vector<Cand> cands;
   for (const auto &v : fpm::variants())
-    if (v.m == p->m && v.smem(rows) <= fpm::kMaxSmem) cands.push_back({FPM_RUN_WAVES, &v, 0.0});
-  cands.push_back({FPM_RUN_PERSISTENT, nullptr, 0.0});
+    if (v.m == p->m && v.smem(rows) <= fpm::kMaxSmem) {
+      const bool first = cands.empty();
+      cands.push_back({FPM_RUN_WAVES, &v, 1, 0.0});
+      if (first)
+        for (int b : {2, 4, 8})
+          if (b <= p->n_tiles) cands.push_back({FPM_RUN_WAVES, &v, b, 0.0});
+    }
+  cands.push_back({FPM_RUN_PERSISTENT, nullptr, 1, 0.0});
   const fpm::Variant *keep = d->var;
+  const int32_t keep_branches = d->branches;
   int rc = FPM_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = fail(FPM_ECUDA, "events");
@@ -1043,6 +1136,7 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
     if (rc) break;
     if (c.v) {
       d->var = c.v;
+      d->branches = c.branches;
       for (auto &kv : d->graphs) cudaGraphExecDestroy(kv.second);   // graphs hold the previous variant
       d->graphs.clear();
     }
@@ -1068,12 +1162,18 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
     int bw = -1;
     for (size_t i = 0; i < cands.size(); ++i)
       if (cands[i].v && (bw < 0 || cands[i].ms < cands[bw].ms)) bw = (int)i;
-    if (bw >= 0) d->var = cands[bw].v;
+    if (bw >= 0) {
+      d->var = cands[bw].v;
+      d->branches = cands[bw].branches;
+    } else {
+      d->branches = keep_branches;
+    }
     d->tuned_mode = cands[bi].mode;
     p->cluster = d->var->c;
     p->threads = d->var->t;
   } else {
     d->var = keep;
+    d->branches = keep_branches;
   }
   // the candidates' wave graphs share one cache key: whichever ran last must not
   // outlive the tuning, so the chosen variant's graph is captured on next use
@@ -1092,6 +1192,7 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
       entries[i].mode = c.mode;
       entries[i].threads = c.v ? c.v->t : fpm::persistent_block_threads(p->m);
       entries[i].cluster = c.v ? c.v->c : 2;
+      entries[i].branches = c.branches;
       entries[i].ms = c.ms;
     }
   if (best) *best = bi;
@@ -1121,6 +1222,16 @@ int fpm_get_spectrum(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, vo
   if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
   const size_t nn = (size_t)p->n * p->n;
   return copy_out(p, p->dev->spec + (size_t)tile * nn, dst, nn * sizeof(float2), on_device, (cudaStream_t)stream);
+}
+
+int fpm_get_spectra(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
+  fpm::clear_error();
+  if (!p || !dst) return fail(FPM_EINVAL, "fpm_get_spectra: null argument");
+  if (!p->dev || !p->dev->loaded) return fail(FPM_ESTATE, "no state before fpm_load_tiles");
+  const size_t bytes = (size_t)p->n_tiles * p->n * p->n * sizeof(float2);
+  FPM_CK(cudaMemcpyAsync(dst, p->dev->spec, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         (cudaStream_t)stream));
+  return FPM_OK;
 }
 
 int fpm_get_pupil(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void *stream) {

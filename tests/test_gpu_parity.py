@@ -280,3 +280,37 @@ def test_fp32_peak_is_near_the_nominal_rate():
     nominal = sms * 128 * 2 * 2.032e9 / 1e12        # 128 FP32 lanes per SM, 2 flop per FMA
     v = fp32_peak()
     assert 0.5 * nominal < v < 1.05 * nominal, (v, nominal)
+
+
+def test_bulk_spectra_getter_matches_per_tile_copies():
+    import torch
+    j = job("m64_epry")
+    p = j.plan(iters=1)
+    p.load_tiles(j.stack, j.counts_per_unit)
+    p.reconstruct(1, mode="waves")
+    host = torch.empty((j.w.n_tiles, p.n, p.n), dtype=torch.complex64, pin_memory=True)
+    dev = torch.empty((j.w.n_tiles, p.n, p.n), dtype=torch.complex64, device="cuda")
+    p.spectra(host)
+    p.spectra(dev)
+    torch.cuda.synchronize()
+    for t in range(j.w.n_tiles):
+        ref = p.spectrum(t)
+        assert np.array_equal(host[t].numpy(), ref) and np.array_equal(dev[t].cpu().numpy(), ref)
+    p.close()
+
+
+def test_graph_branches_over_tile_groups_are_bit_identical(monkeypatch):
+    """Wave steps of disjoint tile groups as parallel graph branches change only the
+    concurrency: 1, 2 and 4 branches give the same state bit for bit."""
+    j = job("m64_epry")
+    outs = []
+    for b in (1, 2, 4):
+        monkeypatch.setenv("FPM_WAVE_BRANCHES", str(b))
+        p = j.plan(iters=2)
+        p.load_tiles(j.stack, j.counts_per_unit)
+        p.reconstruct(2, mode="waves", graph=True)
+        outs.append([p.spectrum(t) for t in range(j.w.n_tiles)] + [p.pupil(t) for t in range(j.w.n_tiles)])
+        p.close()
+    for o in outs[1:]:
+        for a, c in zip(o, outs[0]):
+            assert np.array_equal(a, c)
