@@ -570,15 +570,25 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     run_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    st_timed = plan.stats()          # launch counts of the timed steps' configuration
+    instr_ms = None
     if args.mode != "persistent":
         # per-launch events around each of the step's ~900 update launches cost ~6% of
-        # the step, so they are recorded in one more step after the timed region
-        step(timed=True)
+        # the step (and run the wave steps as one branch), so they are recorded in one
+        # more step after the timed region
+        l0, i0, i1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        l0.record(stream)
+        plan.load_tiles(stack, k)
+        i0.record(stream)
+        plan.reconstruct(w.iters, mode="waves", graph=True, timed=True)
+        i1.record(stream)
         torch.cuda.synchronize()
+        instr_ms = i0.elapsed_time(i1)
+        load_ms = l0.elapsed_time(i0)
     st = plan.stats()
     ms, _, value = aggregate(ms, w.updates * args.steps, dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
-    launches = (st["load_launches"] + st["run_launches"]) * args.steps
+    launches = (st_timed["load_launches"] + st_timed["run_launches"]) * args.steps
 
     # roofline of the dominant kernel, from the CUDA events of the timed region
     fpu, bpu = flops_per_update(w), bytes_per_update(w)
@@ -589,8 +599,10 @@ def main():
     else:
         per_launch_s = st["update_ms"] / 1e3 / st["update_launches"]
         upl, kname, n_launch = st["updates"] / st["update_launches"], "fpm::update_kernel", st["update_launches"]
-        share = st["update_ms"] / ms_per_step
-        kernel_timing = "CUDA events around each update launch of one step run right after the timed region"
+        share = st["update_ms"] / (st["update_ms"] + st["merge_ms"] + load_ms)
+        kernel_timing = ("CUDA events around each update launch of one more step (one graph branch) run right "
+                         "after the timed region; share = update time / (update + merge + load time) of that step, "
+                         "the serialised kernel-time share an ncu launch list gives")
     achieved = fpu * upl / per_launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
@@ -602,7 +614,12 @@ def main():
             "avg_launch_us": per_launch_s * 1e6, "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
             "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9, "kernel_share_of_step": share,
             "peak_source": "measured: fpm_fp32_peak (chains of FFMA on every FP32 lane, this device, this run)",
-            "peak_nominal": FP32_PEAK_TFLOPS, "kernel_timing": kernel_timing}
+            "peak_nominal": FP32_PEAK_TFLOPS, "kernel_timing": kernel_timing,
+            "job_achieved": fpu * w.updates / (run_ms / 1e3) / 1e12,
+            "job_frac": fpu * w.updates / (run_ms / 1e3) / 1e12 / peak,
+            "job_timing": "the job's algorithmic work over the timed steps' reconstruction time (CUDA events "
+                          "around fpm_reconstruct; for wave launches with graph branches the kernels of "
+                          "different tile groups overlap)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 1), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -610,6 +627,8 @@ def main():
             "config": {"workload": w.name, "sensor": w.sensor, "tile": w.tile, "hr": w.hr, "tiles": w.n_tiles,
                        "leds": w.n_leds, "iters": w.iters, "epry": w.epry, "updates_per_step": w.updates,
                        "mode": args.mode + "+graph", "ms_per_fov": ms_per_step, "autotune": tune,
+                       "graph_branches": (tune["entries"][tune["best"]]["branches"] if tune
+                                          else int(os.environ.get("FPM_WAVE_BRANCHES", "1"))),
                        "clusters": st["persistent_clusters"] if args.mode == "persistent" else None,
                        "l2": "inputs larger than L2 (1.9 GB stack, 0.5 GB spectra); no flush",
                        "parallelism": f"{world} independent FOV replicas" if world > 1 else "1 GPU"},

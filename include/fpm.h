@@ -275,6 +275,8 @@ typedef struct {
   int32_t online_launched;  /* wave steps the current or last online ingestion launched */
   int32_t online_steps;     /* wave steps of its schedule                               */
   int32_t pad0;
+  double merge_ms;          /* device time between the end of each timed update launch
+                               and the next launch's start (the wave's pupil merge)     */
 } fpm_stats;
 
 /* fpm_get_stats -- fill *out.  Synchronises the device; update_ms is 0 when no

@@ -188,6 +188,7 @@ struct DeviceState {
   int64_t load_launches = 0, run_launches = 0;
   std::vector<cudaEvent_t> events;            // 2 per wave step of a timed run
   std::vector<int64_t> timed_steps;           // steps whose update launch was timed
+  int64_t timed_n_steps = 0;                  // steps of the timed schedule (its closing event)
   int64_t timed_updates = 0;
   bool timed_valid = false;
   std::map<int32_t, QueueDev *> queues;        // persistent queues by loop count
@@ -605,7 +606,7 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
   int64_t nl = 0;
   if (mode == FPM_RUN_WAVES) {
     if (timed) {
-      while ((int)d->events.size() < 2 * sl.n_steps) {
+      while ((int)d->events.size() < 2 * sl.n_steps + 1) {
         cudaEvent_t ev;
         FPM_CK(cudaEventCreate(&ev));
         d->events.push_back(ev);
@@ -613,6 +614,7 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
       d->timed_steps.clear();
       d->timed_updates = 0;
       d->timed_valid = true;
+      d->timed_n_steps = sl.n_steps;
     }
     for (int s = 0; s < sl.n_steps; ++s) {
       const long long i0 = sl.step_off[s], i1 = sl.step_off[s + 1];
@@ -636,6 +638,9 @@ static int enqueue_reconstruct(fpm_plan *p, int32_t iters, int mode, cudaStream_
         if (m1 > m0) ++nl;
       }
     }
+    if (timed)   // closes the last merge: merges run between an update's end and the next start
+      FPM_CK(capturing ? cudaEventRecordWithFlags(d->events[2 * sl.n_steps], st, cudaEventRecordExternal)
+                       : cudaEventRecord(d->events[2 * sl.n_steps], st));
     FPM_CK(cudaGetLastError());
     *launches = nl;
     return FPM_OK;
@@ -834,14 +839,20 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
   const int derr = device_error(p);
   out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
   if (d->timed_valid && !d->timed_steps.empty()) {
-    FPM_CK(cudaEventSynchronize(d->events[2 * d->timed_steps.back() + 1]));
-    double ms = 0;
-    for (int64_t s : d->timed_steps) {
-      float f = 0.f;
+    const size_t last = d->events.size() > 0 ? (size_t)(2 * d->timed_n_steps) : 0;
+    FPM_CK(cudaEventSynchronize(d->events[last]));
+    double ms = 0, mms = 0;
+    for (size_t k = 0; k < d->timed_steps.size(); ++k) {
+      const int64_t s = d->timed_steps[k];
+      float f = 0.f, g = 0.f;
       FPM_CK(cudaEventElapsedTime(&f, d->events[2 * s], d->events[2 * s + 1]));
+      const cudaEvent_t next = k + 1 < d->timed_steps.size() ? d->events[2 * d->timed_steps[k + 1]] : d->events[last];
+      FPM_CK(cudaEventElapsedTime(&g, d->events[2 * s + 1], next));
       ms += f;
+      mms += g;
     }
     out->update_ms = ms;
+    out->merge_ms = mms;
     out->update_launches = (int64_t)d->timed_steps.size();
     out->updates = d->timed_updates;
   }
@@ -1062,6 +1073,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     const fpm::StepLists &sl = fpm::step_lists(p, iters);
     d->timed_steps.clear();
     d->timed_updates = 0;
+    d->timed_n_steps = sl.n_steps;
     for (int s = 0; s < sl.n_steps; ++s)
       if (sl.step_off[s + 1] > sl.step_off[s]) {
         d->timed_steps.push_back(s);
