@@ -376,10 +376,13 @@ def stitch_timing(plan, torch, dev, stack, k, w, reps=3):
 
 
 def uneven_batch(torch, dev, steps=3):
-    """Three jobs (128/192/256 tiles, 9x9/13x13/15x15 LEDs, 15 loops, EPRY) in one
-    persistent launch per step; returns updates/s and ms per step."""
+    """Three jobs (128/192/256 tiles, 9x9/13x13/15x15 LEDs, 15 loops, EPRY) run together
+    each step: one persistent launch over all their updates, and every job an independent
+    graph branch (its tiles in 4 branches); returns updates/s and ms per step of both."""
     from paper_2203_02507_b300 import plan_for, reconstruct_batch
     ws = [synth.WORKLOADS[k] for k in ("batch_m128", "batch_m192", "batch_m256")]
+    prev = os.environ.get("FPM_WAVE_BRANCHES")
+    os.environ["FPM_WAVE_BRANCHES"] = "4"
     plans, stacks = [], []
     for w in ws:
         p = plan_for(w)
@@ -387,27 +390,36 @@ def uneven_batch(torch, dev, steps=3):
         p.load_tiles(st, k)
         plans.append(p)
         stacks.append((st, k))
+    if prev is None:
+        del os.environ["FPM_WAVE_BRANCHES"]
+    else:
+        os.environ["FPM_WAVE_BRANCHES"] = prev
     upd = sum(w.updates for w in ws)
+    out = {"updates_per_step": upd, "steps": steps, "jobs": [w.name for w in ws]}
+    for mode in ("persistent", "waves"):
+        def step():
+            for p, (st, k) in zip(plans, stacks):
+                p.load_tiles(st, k)
+            reconstruct_batch(plans, [w.iters for w in ws], graph=True, mode=mode)
 
-    def step():
-        for p, (st, k) in zip(plans, stacks):
-            p.load_tiles(st, k)
-        reconstruct_batch(plans, [w.iters for w in ws], graph=True)
-
-    step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
         step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        for p in plans:
+            assert p.stats()["device_error"] == 0
+        out[mode] = {"value": upd / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
     for p in plans:
-        assert p.stats()["device_error"] == 0
         p.close()
-    return {"value": upd / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "updates_per_step": upd, "steps": steps,
-            "jobs": [w.name for w in ws], "mode": "one persistent launch per step (graph)"}
+    out["value"] = out["persistent"]["value"]
+    out["mode"] = ("value: one persistent launch per step (graph); waves: every job a graph branch "
+                   "with its tiles in 4 branches")
+    return out
 
 
 def plain_rate(torch, dev, w):

@@ -220,12 +220,16 @@ FPM_API int fpm_reconstruct(fpm_plan *plan, int32_t iters, int32_t mode, void *s
 
 /*
  * fpm_reconstruct_batch -- run `iters[i]` loops of each of `n` loaded plans
- * together in one persistent launch (tiles of different sizes from different
- * jobs share the device work queue; Sec. 3.1's independent sub-regions).
- * Every plan must be loaded with the same image type.  `mode` is
- * FPM_RUN_PERSISTENT, optionally | FPM_RUN_GRAPH.  Each plan ends exactly as
- * fpm_reconstruct(plan, iters[i]) leaves it.  Errors as fpm_reconstruct;
- * a device-wait timeout is reported by each plan's fpm_get_stats.
+ * together (tiles of different sizes from different jobs; Sec. 3.1's
+ * independent sub-regions).  `mode` FPM_RUN_PERSISTENT: one persistent launch
+ * whose device work queue holds every plan's updates (every plan loaded with
+ * the same image type).  FPM_RUN_WAVES: every plan's wave steps as an
+ * independent branch forked from and joined back into `stream` (split further
+ * into the plan's tile branches, see fpm_autotune).  Either optionally |
+ * FPM_RUN_GRAPH (one graph per distinct batch, cached).  Each plan ends
+ * exactly as fpm_reconstruct(plan, iters[i]) leaves it.  Errors as
+ * fpm_reconstruct; a device-wait timeout is reported by each plan's
+ * fpm_get_stats.
  */
 FPM_API int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t n, int32_t mode,
                                   void *stream);

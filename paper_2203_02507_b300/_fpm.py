@@ -365,12 +365,13 @@ class Server:
             pass
 
 
-def reconstruct_batch(plans, iters=None, graph: bool = False, stream=None):
-    """Run several loaded plans together in one persistent launch (fpm_reconstruct_batch)."""
+def reconstruct_batch(plans, iters=None, graph: bool = False, stream=None, mode: str = "persistent"):
+    """Run several loaded plans together (fpm_reconstruct_batch): mode "persistent" (one
+    persistent launch over all their updates) or "waves" (each plan an independent branch)."""
     n = len(plans)
     hs = (_vp * n)(*[p._h.value for p in plans])
     its = (_i32 * n)(*[int(i) for i in (iters or [p.iters for p in plans])])
-    _check(_lib.fpm_reconstruct_batch(hs, its, n, RUN["persistent"] | (RUN_GRAPH if graph else 0), _stream(stream)))
+    _check(_lib.fpm_reconstruct_batch(hs, its, n, RUN[mode] | (RUN_GRAPH if graph else 0), _stream(stream)))
 
 
 def update_tile_static(spectrum, pupil, image, shift, wavelength_um, na, pixel_um, epry, stream=None):

@@ -199,6 +199,8 @@ struct DeviceState {
   int32_t branches = 1;
   cudaStream_t branch_st[kMaxBranches] = {};
   cudaEvent_t branch_ev[2 * kMaxBranches] = {};
+  cudaStream_t batch_st = nullptr;                 // this plan's part of a wave-mode batch
+  cudaEvent_t batch_ev[2] = {};
 };
 
 static void dfree(void *p) {
@@ -220,6 +222,9 @@ void destroy_device_state(fpm_plan *p) {
   for (cudaStream_t bs : d->branch_st)
     if (bs) cudaStreamDestroy(bs);
   for (cudaEvent_t ev : d->branch_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (d->batch_st) cudaStreamDestroy(d->batch_st);
+  for (cudaEvent_t ev : d->batch_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto &kv : d->queues) free_queue(kv.second);
   forget_batches(p);
@@ -742,10 +747,12 @@ struct BatchKey {
   std::vector<int32_t> iters;
   cudaStream_t st;
   bool graph;
+  int mode = FPM_RUN_PERSISTENT;
   bool operator<(const BatchKey &o) const {
     if (plans != o.plans) return plans < o.plans;
     if (iters != o.iters) return iters < o.iters;
     if (st != o.st) return st < o.st;
+    if (mode != o.mode) return mode < o.mode;
     return graph < o.graph;
   }
 };
@@ -761,12 +768,85 @@ void forget_batches(fpm_plan *p) {
   for (auto it = g_batches.begin(); it != g_batches.end();) {
     if (std::find(it->first.plans.begin(), it->first.plans.end(), p) != it->first.plans.end()) {
       if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
-      free_queue(it->second.q);
+      if (it->second.q) free_queue(it->second.q);
       it = g_batches.erase(it);
     } else {
       ++it;
     }
   }
+}
+
+// Every plan's wave steps on its own stream (each possibly forked into its tile
+// branches), forked from and joined back into st.
+static int enqueue_batch_waves(const std::vector<QueueJob> &jobs, cudaStream_t st, int64_t *launches) {
+  DeviceState *d0 = jobs[0].plan->dev;
+  for (const QueueJob &j : jobs) {
+    DeviceState *d = j.plan->dev;
+    if (!d->batch_st) FPM_CK(cudaStreamCreateWithFlags(&d->batch_st, cudaStreamNonBlocking));
+    for (cudaEvent_t &ev : d->batch_ev)
+      if (!ev) FPM_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  FPM_CK(cudaEventRecord(d0->batch_ev[0], st));             // fork
+  int rc = FPM_OK;
+  for (const QueueJob &j : jobs) {
+    DeviceState *d = j.plan->dev;
+    FPM_CK(cudaStreamWaitEvent(d->batch_st, d0->batch_ev[0], 0));
+    if (rc == FPM_OK) {
+      const int b = std::min(d->branches, std::max(1, j.plan->n_tiles));
+      rc = b > 1 ? enqueue_wave_branches(j.plan, j.iters, b, d->batch_st, launches)
+                 : enqueue_wave_tiles(j.plan, j.iters, 0, j.plan->n_tiles, d->batch_st, launches);
+    }
+    FPM_CK(cudaEventRecord(d->batch_ev[1], d->batch_st));   // join
+    FPM_CK(cudaStreamWaitEvent(st, d->batch_ev[1], 0));
+  }
+  return rc;
+}
+
+// A batch of plans run wave by wave, each plan an independent part of one graph
+// (cached per batch) or, without a graph, of the stream's work.
+int run_batch_waves(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph) {
+  int64_t nl = 0;
+  if (!graph) return enqueue_batch_waves(jobs, st, &nl);
+  BatchKey key;
+  for (const QueueJob &j : jobs) {
+    key.plans.push_back(j.plan);
+    key.iters.push_back(j.iters);
+  }
+  key.st = st;
+  key.graph = true;
+  key.mode = FPM_RUN_WAVES;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  auto it = g_batches.find(key);
+  if (it == g_batches.end()) {
+    for (const QueueJob &j : jobs) {                            // step lists outside the capture
+      const StepLists &sl = step_lists(j.plan, j.iters);
+      int rc = 0;
+      if (!device_steps(j.plan, j.iters, sl, &rc)) return rc;
+    }
+    cudaStream_t cap = st;
+    bool own = false;
+    if (cap == nullptr) {
+      FPM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+    }
+    FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_batch_waves(jobs, cap, &nl);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &gr);
+    if (own) cudaStreamDestroy(cap);
+    if (rc) {
+      if (gr) cudaGraphDestroy(gr);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    BatchEntry be;
+    e = cudaGraphInstantiate(&be.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(FPM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    it = g_batches.emplace(key, be).first;
+  }
+  FPM_CK(cudaGraphLaunch(it->second.exec, st));
+  return FPM_OK;
 }
 
 int run_batch(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph) {
@@ -1090,8 +1170,9 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
 int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t n, int32_t mode, void *stream) {
   fpm::clear_error();
   if (!plans || !iters || n < 1) return fail(FPM_EINVAL, "fpm_reconstruct_batch: empty batch");
-  if ((mode & ~FPM_RUN_GRAPH) != FPM_RUN_PERSISTENT)
-    return fail(FPM_EINVAL, "fpm_reconstruct_batch runs FPM_RUN_PERSISTENT (optionally | FPM_RUN_GRAPH)");
+  const int base = mode & ~FPM_RUN_GRAPH;
+  if (base != FPM_RUN_PERSISTENT && base != FPM_RUN_WAVES)
+    return fail(FPM_EINVAL, "fpm_reconstruct_batch runs FPM_RUN_PERSISTENT or FPM_RUN_WAVES (optionally | FPM_RUN_GRAPH)");
   std::vector<fpm::QueueJob> jobs;
   for (int i = 0; i < n; ++i) {
     fpm_plan *p = plans[i];
@@ -1103,6 +1184,7 @@ int fpm_reconstruct_batch(fpm_plan *const *plans, const int32_t *iters, int32_t 
       if (plans[k] == p) return fail(FPM_EINVAL, "plan %d appears twice", i);
     jobs.push_back(fpm::QueueJob{p, iters[i]});
   }
+  if (base == FPM_RUN_WAVES) return fpm::run_batch_waves(jobs, (cudaStream_t)stream, (mode & FPM_RUN_GRAPH) != 0);
   return fpm::run_batch(jobs, (cudaStream_t)stream, (mode & FPM_RUN_GRAPH) != 0);
 }
 

@@ -21,6 +21,8 @@ int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long lon
 struct QueueJob;
 // One persistent launch over several loaded plans (cached per batch).
 int run_batch(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph);
+// The same batch run wave by wave, every plan an independent branch (of one cached graph).
+int run_batch_waves(const std::vector<QueueJob> &jobs, cudaStream_t st, bool graph);
 // Persistent batched execution of `iters` loops of one plan.
 int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool stall_test);
 

@@ -131,17 +131,21 @@ def test_admission_by_budget_and_overlap():
         p.close()
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_uneven_batch_in_one_persistent_launch(graph):
-    """Four jobs with tiles of 64, 128, 192 and 256 in one launch end exactly as run one by one."""
+@pytest.mark.parametrize("mode,graph", [("persistent", False), ("persistent", True), ("waves", False),
+                                        ("waves", True)])
+def test_uneven_batch_runs_as_one(mode, graph, monkeypatch):
+    """Four jobs with tiles of 64, 128, 192 and 256 run together (one persistent launch, or
+    every plan an independent graph branch split into 2 tile branches) end exactly as run
+    one by one."""
     from paper_2203_02507_b300 import reconstruct_batch
+    monkeypatch.setenv("FPM_WAVE_BRANCHES", "2")
     plans = []
     for w in MIX:
         j = job(w)
         p = j.plan()
         p.load_tiles(j.stack, j.counts_per_unit)
         plans.append(p)
-    reconstruct_batch(plans, [w.iters for w in MIX], graph=graph)
+    reconstruct_batch(plans, [w.iters for w in MIX], graph=graph, mode=mode)
     for w, p in zip(MIX, plans):
         assert p.stats()["device_error"] == 0
         j = job(w)
