@@ -1,7 +1,8 @@
 """Full-size parity: the headline FOV (2048^2 sensor, 64 tiles of 256, 15x15 LEDs,
 EPRY) and the largest single job (5120^2 sensor, 1600 tiles of 128, 21x21 LEDs,
-EPRY, 23 GB of images) run on the GPU in the launch configuration the bench
-times (persistent kernel replayed as a CUDA graph); the oracle recomputes
+EPRY, 23 GB of images) run on the GPU in the launch configurations the bench
+tunes between (wave steps replayed as a CUDA graph with the tiles in 8 parallel
+branches; the persistent kernel replayed as a graph); the oracle recomputes
 sampled tiles one by one.
 
 Tiles are independent (Sec. 3.1), so only the sampled tiles' windows of the
@@ -45,15 +46,20 @@ def _stack_with_samples(w, samples, torch):
     return stack, k, g, dz
 
 
-@pytest.mark.parametrize("name,samples", [("fov2048_m256", [0, 27, 63]), ("fov5120_m128", [0, 841, 1599])])
-def test_full_size_one_loop_sampled_tiles(name, samples):
+@pytest.mark.parametrize("name,samples,mode", [
+    ("fov2048_m256", [0, 27, 63], "waves"), ("fov2048_m256", [0, 27, 63], "persistent"),
+    ("fov5120_m128", [0, 841, 1599], "waves"), ("fov5120_m128", [0, 841, 1599], "persistent")])
+def test_full_size_one_loop_sampled_tiles(name, samples, mode, monkeypatch):
+    """Both launch configurations the bench tunes between: wave-by-wave graph replays with
+    the tiles in 8 parallel branches, and the persistent kernel replayed as a graph."""
     import torch
     from paper_2203_02507_b300 import plan_for
+    monkeypatch.setenv("FPM_WAVE_BRANCHES", "8")
     w = synth.WORKLOADS[name]
     stack, k, g, dz = _stack_with_samples(w, samples, torch)
     p = plan_for(w, defocus_um=dz, iters=1)
     p.load_tiles(stack, k)
-    p.reconstruct(1, mode="persistent", graph=True)
+    p.reconstruct(1, mode=mode, graph=True)
     assert p.stats()["device_error"] == 0
     def window(t):          # the tile's window of the device stack, on the host
         y0, x0 = (int(v) for v in g.origins[t])
