@@ -123,6 +123,11 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), 1) persistent_kern
   // barrier inside the update.
   __shared__ int s_idx[2], s_ok, s_last;
   __shared__ PItem s_item[2];
+  // the current job's arguments, read by the update from shared memory rather
+  // than through a pointer into global memory
+  __shared__ UpdateArgs s_args;
+  static_assert(sizeof(UpdateArgs) % 4 == 0 && sizeof(UpdateArgs) / 4 <= kPT, "one word per thread");
+  int args_job = -1;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned q = cl.block_rank();
   const bool leader = q == 0 && threadIdx.x == 0;
@@ -163,25 +168,32 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), 1) persistent_kern
     }
     cl.sync();
     if (!s_ok) break;
-    // job arguments are read through the pointer and the item re-read from
-    // shared memory after the update, so neither stays in registers across it
-    const JobArgs *jp = pa.jobs + s_item[k].job;
+    // the item is re-read from shared memory after the update, so it does not
+    // stay in registers across it
+    const int job = s_item[k].job;
+    const JobArgs *jp = pa.jobs + job;
+    if (job != args_job) {                 // uniform: every thread read the same item
+      if (threadIdx.x < sizeof(UpdateArgs) / 4)
+        reinterpret_cast<unsigned *>(&s_args)[threadIdx.x] = reinterpret_cast<const unsigned *>(&jp->u)[threadIdx.x];
+      args_job = job;
+      __syncthreads();
+    }
     const int4 item = make_int4(s_item[k].ltile, s_item[k].led, s_item[k].slot, 0);
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     if constexpr (MSEL == 64) {
-      run_update<P64, Img>(jp->u, item, smem, load_tw);
+      run_update<P64, Img>(s_args, item, smem, load_tw);
     } else if constexpr (MSEL == 128) {
-      run_update<P128, Img>(jp->u, item, smem, load_tw);
+      run_update<P128, Img>(s_args, item, smem, load_tw);
     } else if constexpr (MSEL == 192) {
-      run_update<P192, Img>(jp->u, item, smem, load_tw);
+      run_update<P192, Img>(s_args, item, smem, load_tw);
     } else if constexpr (MSEL == 256) {
-      run_update<P256x, Img>(jp->u, item, smem, load_tw);
+      run_update<P256x, Img>(s_args, item, smem, load_tw);
     } else {
       switch (jp->m) {
-        case 64: run_update<P64, Img>(jp->u, item, smem, load_tw); break;
-        case 128: run_update<P128, Img>(jp->u, item, smem, load_tw); break;
-        case 192: run_update<P192, Img>(jp->u, item, smem, load_tw); break;
-        default: run_update<P256, Img>(jp->u, item, smem, load_tw); break;
+        case 64: run_update<P64, Img>(s_args, item, smem, load_tw); break;
+        case 128: run_update<P128, Img>(s_args, item, smem, load_tw); break;
+        case 192: run_update<P192, Img>(s_args, item, smem, load_tw); break;
+        default: run_update<P256, Img>(s_args, item, smem, load_tw); break;
       }
     }
     const PItem done_it = s_item[k];
