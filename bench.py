@@ -42,8 +42,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFL
 # by the updates it processes.  Emptied whenever the kernel changes until
 # re-captured.
 TRAFFIC_PER_UPDATE = {
-    # profiles/persistent_kernel_m256_ncu_full.md: 552,464,128 + 98,662,912 B for 3,600 updates
-    ("persistent", 256): (552464128 + 98662912) / 3600,
+    # profiles/persistent_kernel_m256_ncu_full.md: 552,197,376 + 99,313,664 B for 3,600 updates
+    ("persistent", 256): (552197376 + 99313664) / 3600,
     # profiles/update_kernel_m256_ncu_full.md: 12,489,984 + 0 B for 32 updates
     ("waves", 256): (12489984 + 0) / 32,
 }
