@@ -415,7 +415,10 @@ FPM_API int fpm_fp32_peak(double *tflops, void *stream);
  *   images of type dtype (FPM_U16 / FPM_F32) with intensity = element /
  *   counts_per_unit.  Allocates the plan's device state and tile images as
  *   fpm_load_tiles does, plus four staging images; the plan's previous state is
- *   no longer readable until fpm_online_finish.
+ *   no longer readable until fpm_online_finish.  The wave steps that the last
+ *   image of an ingestion in LED order releases (most of them: waves span
+ *   loops) are captured here as one graph with the tiles in parallel branches,
+ *   launched when that image arrives.
  * fpm_online_push -- the sensor image taken with LED index `led`: sensor_h
  *   rows of sensor_w elements, rows stride_row elements apart.  Host memory
  *   (on_device 0) is copied on the plan's own copy stream; use page-locked

@@ -48,6 +48,10 @@ struct OnlineState {
   cudaEvent_t copied[kOnlineRing] = {}, freed[kOnlineRing] = {};
   bool used[kOnlineRing] = {};
   cudaStream_t copy = nullptr;
+  // the steps the last image of an in-order ingestion releases, captured as a
+  // graph with tile branches at fpm_online_begin
+  cudaGraphExec_t tail = nullptr;
+  int32_t tail_from = -1;
 };
 
 void destroy_online_state(fpm_plan *p) {
@@ -61,6 +65,7 @@ void destroy_online_state(fpm_plan *p) {
     if (o->freed[k]) cudaEventDestroy(o->freed[k]);
   }
   if (o->copy) cudaStreamDestroy(o->copy);
+  if (o->tail) cudaGraphExecDestroy(o->tail);
   delete o;
   p->online = nullptr;
 }
@@ -103,6 +108,11 @@ static int online_advance(fpm_plan *p, cudaStream_t st) {
   int32_t s1 = o->launched;
   while (s1 < (int32_t)o->need.size() && o->need[s1] <= o->prefix) ++s1;
   if (s1 == o->launched) return FPM_OK;
+  if (o->tail && o->launched == o->tail_from && s1 == (int32_t)o->need.size()) {
+    FPM_CK(cudaGraphLaunch(o->tail, st));
+    o->launched = s1;
+    return FPM_OK;
+  }
   const int rc = enqueue_wave_steps(p, o->iters, o->launched, s1, st);
   if (rc == FPM_OK) o->launched = s1;
   return rc;
@@ -147,6 +157,15 @@ int fpm_online_begin(fpm_plan *p, int32_t iters, int32_t dtype, float counts_per
       run = std::max(run, o->pos[sl.items[i * 4 + 1]] + 1);
     o->need[s] = run;
   }
+  // in LED order the last image releases every step that needs all of them
+  if (o->tail) {
+    cudaGraphExecDestroy(o->tail);
+    o->tail = nullptr;
+  }
+  o->tail_from = (int32_t)(std::lower_bound(o->need.begin(), o->need.end(), p->n_leds) - o->need.begin());
+  if (o->tail_from < sl.n_steps &&
+      (rc = fpm::capture_wave_steps(p, iters, o->tail_from, sl.n_steps, 8, &o->tail)))
+    return rc;
   o->active = true;
   return FPM_OK;
 }

@@ -504,9 +504,47 @@ int plan_scratch(fpm_plan *p, size_t bytes, void **out) {
 
 // Enqueue the launches of `iters` loops in the given mode; *launches counts kernels.
 // With `timed`, CUDA events bracket every update launch (waves mode only).
+static int enqueue_wave_branches(fpm_plan *p, int32_t iters, int s0, int s1, int branches, cudaStream_t st,
+                                 int64_t *launches);
+static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int s0, int s1, int t0, int t1, cudaStream_t st,
+                              int64_t *launches);
+
+// Wave steps [s0, s1) captured as one graph of `branches` tile-group branches.
+int capture_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, int branches, cudaGraphExec_t *out) {
+  *out = nullptr;
+  const StepLists &sl = step_lists(p, iters);
+  int rc = 0;
+  if (!device_steps(p, iters, sl, &rc)) return rc;            // uploads stay outside the capture
+  cudaStream_t cap = nullptr;
+  FPM_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  int64_t nl = 0;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const int b = std::min(branches, std::max(1, p->n_tiles));
+    rc = b > 1 ? enqueue_wave_branches(p, iters, s0, s1, b, cap, &nl)
+               : enqueue_wave_tiles(p, iters, s0, s1, 0, p->n_tiles, cap, &nl);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cap);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "capture of wave steps: %s", cudaGetErrorString(e));
+  return FPM_OK;
+}
+
 // Wave steps [s0, s1) of the `iters`-loop schedule, as FPM_RUN_WAVES runs them:
-// each step's update launch, then (EPRY) its pupil merge.
+// each step's update launch, then (EPRY) its pupil merge; with the plan's
+// branch count above 1, two tile groups' parts as parallel branches (launched
+// one by one, not replayed as a graph: more branches make the host's launch
+// rate the limit).
 int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t st) {
+  const int b = std::min(std::min(p->dev->branches, 2), std::max(1, p->n_tiles));
+  if (b > 1) {
+    int64_t nl = 0;
+    return enqueue_wave_branches(p, iters, s0, s1, b, st, &nl);
+  }
   const StepLists &sl = step_lists(p, iters);
   int rc = 0;
   const StepDev *sd = device_steps(p, iters, sl, &rc);
@@ -528,9 +566,10 @@ int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t 
   return FPM_OK;
 }
 
-// All wave steps of the `iters`-loop schedule restricted to tiles [t0, t1) (a
-// step's items and merges are sorted by tile, so the range is contiguous).
-static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int t0, int t1, cudaStream_t st, int64_t *launches) {
+// Wave steps [s0, s1) of the `iters`-loop schedule restricted to tiles [t0, t1)
+// (a step's items and merges are sorted by tile, so the range is contiguous).
+static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int s0, int s1, int t0, int t1, cudaStream_t st,
+                              int64_t *launches) {
   const StepLists &sl = step_lists(p, iters);
   int rc = 0;
   const StepDev *sd = device_steps(p, iters, sl, &rc);
@@ -556,7 +595,7 @@ static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int t0, int t1, cudaSt
     return lo;
   };
   int64_t nl = 0;
-  for (int s = 0; s < sl.n_steps; ++s) {
+  for (int s = std::max(0, s0); s < std::min(s1, sl.n_steps); ++s) {
     const int64_t i0 = first_item(sl.step_off[s], sl.step_off[s + 1], t0);
     const int64_t i1 = first_item(i0, sl.step_off[s + 1], t1);
     if (i1 == i0) continue;
@@ -576,9 +615,10 @@ static int enqueue_wave_tiles(fpm_plan *p, int32_t iters, int t0, int t1, cudaSt
   return FPM_OK;
 }
 
-// The wave steps as `branches` parallel branches over tile groups: forked from
-// and joined back into the (capturing) stream st with events.
-static int enqueue_wave_branches(fpm_plan *p, int32_t iters, int branches, cudaStream_t st, int64_t *launches) {
+// Wave steps [s0, s1) as `branches` parallel branches over tile groups: forked
+// from and joined back into the stream st (capturing or not) with events.
+static int enqueue_wave_branches(fpm_plan *p, int32_t iters, int s0, int s1, int branches, cudaStream_t st,
+                                 int64_t *launches) {
   DeviceState *d = p->dev;
   for (int k = 0; k < branches; ++k) {
     if (k > 0 && !d->branch_st[k]) FPM_CK(cudaStreamCreateWithFlags(&d->branch_st[k], cudaStreamNonBlocking));
@@ -590,7 +630,7 @@ static int enqueue_wave_branches(fpm_plan *p, int32_t iters, int branches, cudaS
   int rc = FPM_OK;
   for (int k = 0; k < branches && rc == FPM_OK; ++k) {
     const int t0 = (int)((int64_t)p->n_tiles * k / branches), t1 = (int)((int64_t)p->n_tiles * (k + 1) / branches);
-    rc = enqueue_wave_tiles(p, iters, t0, t1, k == 0 ? st : d->branch_st[k], launches);
+    rc = enqueue_wave_tiles(p, iters, s0, s1, t0, t1, k == 0 ? st : d->branch_st[k], launches);
   }
   for (int k = 1; k < branches; ++k) {                          // join (also after a failure, to end the capture cleanly)
     FPM_CK(cudaEventRecord(d->branch_ev[2 * k + 1], d->branch_st[k]));
@@ -793,8 +833,8 @@ static int enqueue_batch_waves(const std::vector<QueueJob> &jobs, cudaStream_t s
     FPM_CK(cudaStreamWaitEvent(d->batch_st, d0->batch_ev[0], 0));
     if (rc == FPM_OK) {
       const int b = std::min(d->branches, std::max(1, j.plan->n_tiles));
-      rc = b > 1 ? enqueue_wave_branches(j.plan, j.iters, b, d->batch_st, launches)
-                 : enqueue_wave_tiles(j.plan, j.iters, 0, j.plan->n_tiles, d->batch_st, launches);
+      rc = b > 1 ? enqueue_wave_branches(j.plan, j.iters, 0, 1 << 30, b, d->batch_st, launches)
+                 : enqueue_wave_tiles(j.plan, j.iters, 0, 1 << 30, 0, j.plan->n_tiles, d->batch_st, launches);
     }
     FPM_CK(cudaEventRecord(d->batch_ev[1], d->batch_st));   // join
     FPM_CK(cudaStreamWaitEvent(st, d->batch_ev[1], 0));
@@ -1130,7 +1170,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     }
     FPM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     int64_t nl = 0;
-    if (branches > 1) rc = fpm::enqueue_wave_branches(p, iters, branches, cap, &nl);
+    if (branches > 1) rc = fpm::enqueue_wave_branches(p, iters, 0, 1 << 30, branches, cap, &nl);
     else rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
     d->graph_launches[key] = nl;
     d->graph_threads[key] = d->var->t;

@@ -49,6 +49,8 @@ int gather_tile_images(fpm_plan *p, const void *src, int32_t dtype, long long st
 // Initial guess of every tile from `plane`, the sensor image of the order's first
 // LED (rows stride_row elements apart); resets the pupils.  Uses the plan's dtype.
 int run_init(fpm_plan *p, const void *plane, long long stride_row, cudaStream_t st);
+// Wave steps [s0, s1) captured as one graph of `branches` tile-group branches.
+int capture_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, int branches, cudaGraphExec_t *out);
 // Wave steps [s0, s1) of the `iters`-loop schedule, launched as FPM_RUN_WAVES does.
 int enqueue_wave_steps(fpm_plan *p, int32_t iters, int s0, int s1, cudaStream_t st);
 // Set the plan's image type and intensity scale and clear its error word (before a load).

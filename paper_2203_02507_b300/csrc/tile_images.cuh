@@ -26,11 +26,23 @@ __global__ void tile_images_kernel(Img *out, const Img *stack, long long stride_
     const int2 o = origins[t];
     const Img *src = stack + (long long)l * stride_led + (long long)o.x * stride_row + o.y + x0;
     __syncthreads();   // the previous block's reads of col_buf are done
-    for (int i = threadIdx.x; i < m * 32; i += blockDim.x) {
-      const int y = i >> 5, x = i & 31;
-      const Img v = src[(long long)y * stride_row + x];
-      if constexpr (sizeof(Img) == 2) col_buf[y * 33 + x] = (unsigned)v;
-      else col_buf[y * 33 + x] = __float_as_uint(v);
+    // kLoads independent loads per thread in flight before their shared-memory stores
+    constexpr int kLoads = 16;
+    for (int i0 = threadIdx.x; i0 < m * 32; i0 += blockDim.x * kLoads) {
+      Img v[kLoads];
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < m * 32) v[u] = src[(long long)(i >> 5) * stride_row + (i & 31)];
+      }
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < m * 32) {
+          if constexpr (sizeof(Img) == 2) col_buf[(i >> 5) * 33 + (i & 31)] = (unsigned)v[u];
+          else col_buf[(i >> 5) * 33 + (i & 31)] = __float_as_uint(v[u]);
+        }
+      }
     }
     __syncthreads();
     Img *dst = out + tile_image_offset(t, led0 + l, n_leds, m) + (size_t)x0 * m;

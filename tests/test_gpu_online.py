@@ -39,11 +39,13 @@ def offline(j, w):
 
 
 @pytest.mark.parametrize("w", JOBS, ids=[w.name for w in JOBS])
-@pytest.mark.parametrize("how", ["in_order", "shuffled", "device"])
-def test_online_equals_offline(w, how):
+@pytest.mark.parametrize("how", ["in_order", "shuffled", "device", "branches"])
+def test_online_equals_offline(w, how, monkeypatch):
     import torch
     j = job(w)
     ref = offline(j, w)
+    if how == "branches":                      # ready steps launched as two tile branches
+        monkeypatch.setenv("FPM_WAVE_BRANCHES", "2")
     p = j.plan()
     order = p.schedule()["order"]
     seq = list(order)
