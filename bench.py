@@ -644,7 +644,10 @@ def main():
                        "clusters": st["persistent_clusters"] if args.mode == "persistent" else None,
                        "l2": "inputs larger than L2 (1.9 GB stack, 0.5 GB spectra); no flush",
                        "parallelism": f"{world} independent FOV replicas" if world > 1 else "1 GPU"},
-            "roofline": roof, "gpu_launches": launches, "clocks": clk}
+            "roofline": roof, "gpu_launches": launches, "clocks": clk,
+            "step_parts": {"reconstruct_ms": run_ms, "load_ms": ms_per_step - run_ms,
+                           "how": "CUDA events around fpm_reconstruct in every timed step; load = the rest of "
+                                  "the step (fpm_load_tiles: tile-image gather and initial guess)"}}
 
     if not args.no_extras and rank == 0:
         # e2e through the public API with host buffers: per FOV the H2D of its stack (page-locked),

@@ -125,7 +125,8 @@ typedef struct {
   int32_t max_wave_width;       /* largest number of LEDs in one wave of one tile      */
   int64_t total_waves;          /* sum over tiles of their wave counts                 */
   int64_t device_bytes;         /* device memory of the state fpm_load_tiles allocates
-                                   (spectra, pupils, corrections), tile images apart   */
+                                   (spectra, pupils and initial pupils, corrections),
+                                   tile images apart                                    */
   int32_t cluster;              /* CTAs that share one update (1 or 2)                 */
   int32_t threads;              /* threads per CTA of the update kernel                */
   int64_t image_elems;          /* elements of the tile images fpm_load_tiles keeps
@@ -300,7 +301,7 @@ typedef struct {
 /*
  * fpm_autotune -- time every execution path that fits the plan's tile side
  * (wave-by-wave launches with each update-kernel variant -- threads per CTA,
- * CTAs per SM -- and, for the first variant, with the tiles split into 2, 4
+ * CTAs per cluster and per SM -- each also with the tiles split into 2, 4
  * and 8 groups whose wave steps run as parallel graph branches; and the persistent
  * kernel) on `iters` loops of the plan's own
  * loaded data, each replayed as a CUDA graph after a warm-up, and keep the

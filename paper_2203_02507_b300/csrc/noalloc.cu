@@ -143,9 +143,7 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   float2 *pup = static_cast<float2 *>(pupil);
 
   // 0. the image in the update kernel's column layout
-  fpm::tile_images_kernel<float><<<m / 32, 256, (size_t)m * 33 * sizeof(unsigned), st>>>(
-      d_img, image, (long long)m * m, m, d_sh + 1, m, fa, fb, 1, 0, 1, m / 32);
-  e = cudaGetLastError();
+  e = fpm::launch_tile_images(d_img, image, (long long)m * m, m, d_sh + 1, m, 1, 1, 0, 1, st);
   if (e != cudaSuccess) return fail(FPM_ECUDA, "image layout: %s", cudaGetErrorString(e));
 
   // 1. zero the correction (the merge sums whole pixel pairs, so entries off this

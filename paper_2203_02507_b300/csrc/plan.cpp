@@ -418,7 +418,7 @@ int fpm_plan_get_info(const fpm_plan *p, fpm_plan_info *info) {
   info->max_wave_width = p->max_width;
   info->total_waves = p->total_waves;
   const int64_t T = p->n_tiles, n = p->n, m = p->m;
-  info->device_bytes = T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + p->max_width : 1);
+  info->device_bytes = T * n * n * 8 + T * m * m * 8 * (p->epry ? 2 + p->max_width : 2);
   info->cluster = p->cluster;
   info->threads = p->threads;
   info->image_elems = T * p->n_leds * m * m;

@@ -53,11 +53,12 @@ using Cfg192c = UpdateCfg<192, 12, 16, 16, 2, 256, 1>;
 using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
+using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),
                                          make_variant<Cfg128w>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),
-                                         make_variant<Cfg256x>(),
+                                         make_variant<Cfg256x>(), make_variant<Cfg256q>(),
                                          make_variant<Cfg256w>(), make_variant<Cfg256>()};
   return v;
 }
@@ -166,6 +167,7 @@ constexpr int kMaxBranches = 8;
 struct DeviceState {
   int device = -1;
   float2 *spec = nullptr, *pup = nullptr, *dpup = nullptr;   // pup: [T][m][m]; dpup: [T][W][m][m]
+  float2 *pup0 = nullptr;                           // initial pupils [T][m][m] (each load starts from them)
   int2 *shifts = nullptr, *origins = nullptr, *chords = nullptr;
   float2 *tw_inv = nullptr, *tw_fwd = nullptr;      // update kernel split
   float2 *twl_fwd_m = nullptr;                      // line FFT tables
@@ -232,7 +234,7 @@ void destroy_device_state(fpm_plan *p) {
     dfree(s.items);
     dfree(s.merges);
   }
-  for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
+  for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->pup0, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
                   (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
                   d->images, d->scratch})
     dfree(q);
@@ -269,6 +271,9 @@ int ensure_device_state(fpm_plan *p) {
   if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess)
     return fail(FPM_ENOMEM, "device allocation of the tile state failed: %s", cudaGetErrorString(e));
+  if ((e = cudaMalloc((void **)&d->pup0, T * m * m * sizeof(float2))) != cudaSuccess)
+    return fail(FPM_ENOMEM, "device allocation of the initial pupils failed: %s", cudaGetErrorString(e));
+  FPM_CK(cudaMemcpy(d->pup0, p->pupil0.data(), T * m * m * sizeof(float2), cudaMemcpyHostToDevice));
   if (p->epry) {
     const size_t db = T * (size_t)p->max_width * m * m * sizeof(float2);
     if ((e = cudaMalloc((void **)&d->dpup, db)) != cudaSuccess)
@@ -380,7 +385,7 @@ int run_init(fpm_plan *p, const void *plane, long long stride_row, cudaStream_t 
   FPM_CK(cudaGetLastError());
   FPM_CK(cudaFreeAsync(tmp, st));
   // pupils into buffer 0
-  FPM_CK(cudaMemcpyAsync(d->pup, p->pupil0.data(), (size_t)T * m * m * sizeof(float2), cudaMemcpyHostToDevice, st));
+  FPM_CK(cudaMemcpyAsync(d->pup, d->pup0, (size_t)T * m * m * sizeof(float2), cudaMemcpyDeviceToDevice, st));
   d->load_launches = 5;   // tile images, gather, 2 x line FFT, place
   return FPM_OK;
 }
@@ -1043,19 +1048,13 @@ int ensure_images(fpm_plan *p, int32_t dtype) {
 int gather_tile_images(fpm_plan *p, const void *src, int32_t dtype, long long stride_led, long long stride_row,
                        int led0, int n_src, cudaStream_t st) {
   DeviceState *d = p->dev;
-  const int m = p->m;
-  const long long n_blocks = (long long)p->n_tiles * n_src * (m / 32);
-  const unsigned grid = (unsigned)std::min<long long>(n_blocks, 148LL * 16);
-  const size_t smem = (size_t)m * 33 * sizeof(unsigned);
-  if (dtype == FPM_U16)
-    tile_images_kernel<uint16_t><<<grid, 256, smem, st>>>((uint16_t *)d->images, (const uint16_t *)src, stride_led,
-                                                          stride_row, d->origins, m, d->var->a, d->var->b, p->n_leds,
-                                                          led0, n_src, n_blocks);
-  else
-    tile_images_kernel<float><<<grid, 256, smem, st>>>((float *)d->images, (const float *)src, stride_led, stride_row,
-                                                       d->origins, m, d->var->a, d->var->b, p->n_leds, led0, n_src,
-                                                       n_blocks);
-  FPM_CK(cudaGetLastError());
+  const cudaError_t e =
+      dtype == FPM_U16
+          ? launch_tile_images((uint16_t *)d->images, (const uint16_t *)src, stride_led, stride_row, d->origins, p->m,
+                               p->n_tiles, p->n_leds, led0, n_src, st)
+          : launch_tile_images((float *)d->images, (const float *)src, stride_led, stride_row, d->origins, p->m,
+                               p->n_tiles, p->n_leds, led0, n_src, st);
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "tile image gather: %s", cudaGetErrorString(e));
   return FPM_OK;
 }
 
@@ -1115,7 +1114,7 @@ size_t image_bytes(const fpm_plan *p, int32_t dtype) {
 
 size_t plan_device_bytes(const fpm_plan *p, int32_t dtype) {
   const size_t T = p->n_tiles, n = p->n, m = p->m;
-  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 1 + (size_t)p->max_width : 1) + image_bytes(p, dtype);
+  return T * n * n * 8 + T * m * m * 8 * (p->epry ? 2 + (size_t)p->max_width : 2) + image_bytes(p, dtype);
 }
 
 }  // namespace fpm
@@ -1251,11 +1250,9 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
   std::vector<Cand> cands;
   for (const auto &v : fpm::variants())
     if (v.m == p->m && v.smem(rows) <= fpm::kMaxSmem) {
-      const bool first = cands.empty();
       cands.push_back({FPM_RUN_WAVES, &v, 1, 0.0});
-      if (first)
-        for (int b : {2, 4, 8})
-          if (b <= p->n_tiles) cands.push_back({FPM_RUN_WAVES, &v, b, 0.0});
+      for (int b : {2, 4, 8})
+        if (b <= p->n_tiles) cands.push_back({FPM_RUN_WAVES, &v, b, 0.0});
     }
   cands.push_back({FPM_RUN_PERSISTENT, nullptr, 1, 0.0});
   const fpm::Variant *keep = d->var;

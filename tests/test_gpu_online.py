@@ -104,3 +104,24 @@ def test_online_misuse_is_refused():
         p.spectrum(0)                                          # state not readable mid-ingestion
     assert e.value.code == ESTATE
     p.close()
+
+
+def test_strided_device_pushes_equal_offline():
+    """Device images whose rows are an odd number of pixels apart are gathered
+    pixel by pixel; the offline load of the same images moves 16-byte words.
+    Both give the same state bit for bit."""
+    import torch
+    w = JOBS[1]
+    j = job(w)
+    ref = offline(j, w)
+    p = j.plan()
+    p.online_begin(w.iters, dtype="u16", counts_per_unit=j.counts_per_unit)
+    h, wd = j.stack.shape[1:]
+    for led in p.schedule()["order"]:
+        big = torch.zeros((h, wd + 3), dtype=torch.int16, device="cuda")
+        big[:, :wd] = torch.from_numpy(j.stack[led].view(np.int16)).cuda()
+        p.online_push(int(led), big[:, :wd])
+    p.online_finish()
+    for a, b in zip(state(p, w), ref):
+        assert np.array_equal(a, b)
+    p.close()

@@ -42,6 +42,12 @@ SMALL = {
                                 optics=O9, defocus_um=(-20.0, 20.0), seed_offset=3000),
     "m256_fixed_f32": synth.Workload("m256_fixed_f32", sensor=256, tile=256, tiles=1, overlap=0, iters=2,
                                      epry=False, optics=O9, image_dtype="f32"),
+    # tile columns start off a 16-byte boundary (origins 42 and 93): the tile
+    # images are gathered pixel by pixel instead of in 16-byte words
+    "m64_odd": synth.Workload("m64_odd", sensor=200, tile=64, tiles=2, overlap=13, iters=2, epry=True,
+                              optics=O9, defocus_um=(-20.0, 20.0), seed_offset=9700),
+    "m64_odd_f32": synth.Workload("m64_odd_f32", sensor=200, tile=64, tiles=2, overlap=13, iters=2, epry=True,
+                                  optics=O9, defocus_um=(-20.0, 20.0), seed_offset=9800, image_dtype="f32"),
 }
 _JOBS = {}
 
@@ -120,7 +126,7 @@ def test_single_update_matches_oracle(m, epry):
 
 
 @pytest.mark.parametrize("name", ["tile64_plain", "m64_epry9", "m64_epry", "m128_epry", "m192_epry", "m256_epry",
-                                  "m256_fixed_f32"])
+                                  "m256_fixed_f32", "m64_odd", "m64_odd_f32"])
 def test_one_iteration_matches_oracle(name):
     j = job(name)
     p = j.plan(iters=1)
@@ -310,6 +316,25 @@ def test_graph_branches_over_tile_groups_are_bit_identical(monkeypatch):
         p.load_tiles(j.stack, j.counts_per_unit)
         p.reconstruct(2, mode="waves", graph=True)
         outs.append([p.spectrum(t) for t in range(j.w.n_tiles)] + [p.pupil(t) for t in range(j.w.n_tiles)])
+        p.close()
+    for o in outs[1:]:
+        for a, c in zip(o, outs[0]):
+            assert np.array_equal(a, c)
+
+
+def test_update_kernel_variants_are_bit_identical(monkeypatch):
+    """Every update-kernel variant of a tile side (threads per CTA, CTAs per
+    cluster) runs the same per-row and per-column arithmetic: the same state bit
+    for bit, whichever variant the autotuner picks."""
+    j = job("m256_epry")
+    outs = []
+    for t in (448, 384, 256, 192):                      # 192: four-CTA clusters, two CTAs per SM
+        monkeypatch.setenv("FPM_UPDATE_THREADS", str(t))
+        p = j.plan(iters=2)
+        p.load_tiles(j.stack, j.counts_per_unit)
+        p.reconstruct(2, mode="waves", graph=True)
+        assert p.stats()["run_threads"] == t
+        outs.append([p.spectrum(t_) for t_ in range(j.w.n_tiles)] + [p.pupil(t_) for t_ in range(j.w.n_tiles)])
         p.close()
     for o in outs[1:]:
         for a, c in zip(o, outs[0]):
