@@ -37,15 +37,17 @@ UNIT = "updates/s"
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
 
-# DRAM bytes per update ((mode, m) -> bytes) of the dominant kernel, from the
-# latest ncu capture in profiles/ of the kernel as it stands; a launch scales it
-# by the updates it processes.  Emptied whenever the kernel changes until
-# re-captured.
+# DRAM bytes per update ((mode, m, threads per CTA) -> bytes) of the dominant
+# kernel, from the latest ncu capture in profiles/ of the kernel as it stands; a
+# launch scales it by the updates it processes.  Emptied whenever the kernel
+# changes until re-captured.
 TRAFFIC_PER_UPDATE = {
     # profiles/persistent_kernel_m256_ncu_full.md: 552,197,376 + 99,313,664 B for 3,600 updates
-    ("persistent", 256): (552197376 + 99313664) / 3600,
+    ("persistent", 256, 448): (552197376 + 99313664) / 3600,
     # profiles/update_kernel_m256_ncu_full.md: 12,489,984 + 0 B for 32 updates
-    ("waves", 256): (12489984 + 0) / 32,
+    ("waves", 256, 448): (12489984 + 0) / 32,
+    # profiles/update_kernel_m256_c4_ncu_full.md: 12,492,288 + 256 B for 32 updates
+    ("waves", 256, 192): (12492288 + 256) / 32,
 }
 
 EXTRA = {
@@ -618,8 +620,8 @@ def main():
     achieved = fpu * upl / per_launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": (TRAFFIC_PER_UPDATE[(args.mode, w.tile)] * upl
-                        if (args.mode, w.tile) in TRAFFIC_PER_UPDATE else None),
+            "traffic": (TRAFFIC_PER_UPDATE[(args.mode, w.tile, st["run_threads"])] * upl
+                        if (args.mode, w.tile, st["run_threads"]) in TRAFFIC_PER_UPDATE else None),
             "traffic_source": "ncu dram__bytes_read+write per update on a 16-tile case (profiles/), "
                               "scaled by this launch's updates",
             "kernel": kname, "launches_per_step": n_launch, "updates_per_launch": upl,

@@ -53,7 +53,7 @@ using Cfg192c = UpdateCfg<192, 12, 16, 16, 2, 256, 1>;
 using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
-using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2>;
+using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2, 1, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),

@@ -79,9 +79,11 @@ struct ImgCol {
 
 // PF_ = 1: a lane loads its next column's image pixels one column ahead;
 // 0: at the start of the column (8 registers fewer for 16-bit images, 16 for float).
-template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1>
+// PR_ = 1: a lane loads its next support row's spectrum and pupil values during
+// the second pass of the current row (4 A registers more); 0: at the row's start.
+template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0>
 struct UpdateCfg {
-  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_;
+  static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_, PR = PR_;
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -159,8 +161,12 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   __syncthreads();
 
   // ---- phase 1: IDFT along x of every support row -------------------------
+  // A lane's spectrum and pupil values of its next row are loaded while the
+  // second pass of the current row runs (Cfg::PR), so their latency overlaps
+  // that pass instead of opening every row.
   float omax = 0.f, pmax = 0.f;
-  for (int i = r0 + g; i < r1; i += G) {
+  float2 ov1[Cfg::UA][A], pv1[Cfg::UA][A];
+  auto load_row = [&](int i) {
     const int by = a.y_lo + i;
     const int2 ch = a.chords[by];
     const float2 *__restrict__ srow = spec + (size_t)by * n;
@@ -168,20 +174,29 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
     for (int u = 0; u < Cfg::UA; ++u) {
       const int b = tl + u * TPT;
-      if (b < B) {
-        float2 v[A], pv[A];
 #pragma unroll
-        for (int aa = 0; aa < A; ++aa) {     // all loads first
-          const int x = B * aa + b;
-          const bool in = x >= ch.x && x <= ch.y;
-          v[aa] = in ? srow[x] : make_float2(0.f, 0.f);
-          pv[aa] = in ? prow[x] : make_float2(0.f, 0.f);
-        }
+      for (int aa = 0; aa < A; ++aa) {
+        const int x = B * aa + b;
+        const bool in = b < B && x >= ch.x && x <= ch.y;
+        ov1[u][aa] = in ? srow[x] : make_float2(0.f, 0.f);
+        pv1[u][aa] = in ? prow[x] : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  if (Cfg::PR && r0 + g < r1) load_row(r0 + g);
+  for (int i = r0 + g; i < r1; i += G) {
+    const int by = a.y_lo + i;
+    if constexpr (!Cfg::PR) load_row(i);
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int b = tl + u * TPT;
+      if (b < B) {
+        float2 v[A];
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) {
-          omax = fmaxf(omax, cabs2(v[aa]));
-          pmax = fmaxf(pmax, cabs2(pv[aa]));
-          v[aa] = cmul(v[aa], pv[aa]);
+          omax = fmaxf(omax, cabs2(ov1[u][aa]));
+          pmax = fmaxf(pmax, cabs2(pv1[u][aa]));
+          v[aa] = cmul(ov1[u][aa], pv1[u][aa]);
         }
         Dft<A, 1>::run(v);
 #pragma unroll
@@ -192,6 +207,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       }
     }
     __syncwarp(gmask);
+    if constexpr (Cfg::PR) {
+      if (i + G < r1) load_row(i + G);
+    }
 #pragma unroll
     for (int u = 0; u < Cfg::UB; ++u) {
       const int k1 = tl + u * TPT;
