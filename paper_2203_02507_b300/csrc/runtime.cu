@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -54,11 +55,12 @@ using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
 using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2, 1, 1>;
+using Cfg256o = UpdateCfg<256, 16, 16, 16, 4, 256, 2, 1, 0, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),
                                          make_variant<Cfg128w>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),
-                                         make_variant<Cfg256x>(), make_variant<Cfg256q>(),
+                                         make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256o>(),
                                          make_variant<Cfg256w>(), make_variant<Cfg256>()};
   return v;
 }
@@ -66,12 +68,15 @@ static const std::vector<Variant> &variants() {
 static constexpr size_t kMaxSmem = 232448;   // 227 KB per CTA on sm_103a
 
 // First candidate for tile side m whose shared memory fits; FPM_UPDATE_THREADS
-// (environment) restricts the choice to one thread count.
+// (environment) restricts the choice to one thread count ("448") or to one
+// thread count and cluster size ("256x4").
 static const Variant *find_variant(int m, int rows) {
   const char *env = getenv("FPM_UPDATE_THREADS");
-  const int want = env ? atoi(env) : 0;
+  int want = 0, want_c = 0;
+  if (env && sscanf(env, "%dx%d", &want, &want_c) < 1) want = 0;
   for (const auto &v : variants())
-    if (v.m == m && v.smem(rows) <= kMaxSmem && (want == 0 || v.t == want)) return &v;
+    if (v.m == m && v.smem(rows) <= kMaxSmem && (want == 0 || v.t == want) && (want_c == 0 || v.c == want_c))
+      return &v;
   for (const auto &v : variants())
     if (v.m == m && v.smem(rows) <= kMaxSmem) return &v;
   return nullptr;

@@ -81,9 +81,12 @@ struct ImgCol {
 // 0: at the start of the column (8 registers fewer for 16-bit images, 16 for float).
 // PR_ = 1: a lane loads its next support row's spectrum and pupil values during
 // the second pass of the current row (4 A registers more); 0: at the row's start.
-template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0>
+// TG_ = 1: the twiddles are read from global memory (they stay in L1) instead of
+// shared memory, 4 KB less shared memory per CTA at m = 256.
+template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0, int TG_ = 0>
 struct UpdateCfg {
   static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_, PR = PR_;
+  static constexpr int TG = TG_;
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -96,14 +99,22 @@ struct UpdateCfg {
   static_assert(T <= 512, "the normaliser holds one partial per warp in 16 slots");
   // shared memory in bytes for R support rows
   static size_t smem_bytes(int rows) {
-    return ((size_t)rows * W + (size_t)G * SCR + 2 * M) * sizeof(float2) + 64 * sizeof(float);
+    return ((size_t)rows * W + (size_t)G * SCR + (TG ? 0 : 2 * M)) * sizeof(float2) + 64 * sizeof(float);
   }
 };
+
+// Twiddle i of a table: a shared-memory load, or a read-only global load (Cfg::TG).
+template <class Cfg>
+__device__ __forceinline__ float2 tw_at(const float2 *t, int i) {
+  if constexpr (Cfg::TG) return __ldg(t + i);
+  else return t[i];
+}
 
 // The transform twiddles of tile side M into the start of shared memory (the
 // caller synchronises before run_update reads them).
 template <class Cfg>
 __device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem) {
+  if constexpr (Cfg::TG) return;
   for (int i = threadIdx.x; i < Cfg::M; i += Cfg::T) {
     smem[i] = a.tw_inv[i];
     smem[Cfg::M + i] = a.tw_fwd[i];
@@ -111,17 +122,18 @@ __device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem)
 }
 
 // One update; all threads of all C CTAs of the cluster call this with the same item.
-// Shared memory: [twiddles 2m][normaliser partials][inter R x W][exchange scratch].
+// Shared memory: [twiddles 2m (not with Cfg::TG)][normaliser partials][inter R x W][exchange scratch].
 // load_tw = false keeps the twiddles of an earlier update with the same m.
 template <class Cfg, typename Img>
 __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem, bool load_tw = true) {
   constexpr int M = Cfg::M, A = Cfg::A, B = Cfg::B, TPT = Cfg::TPT, C = Cfg::C, T = Cfg::T;
   constexpr int W = Cfg::W, G = Cfg::G, SCR = Cfg::SCR;
   const int rows = a.rows;
-  float2 *twi = smem;
-  float2 *twf = twi + M;
-  float *red = reinterpret_cast<float *>(twf + M);
-  float2 *inter = twf + M + 32;             // after 64 floats of partials
+  const float2 *twi = Cfg::TG ? a.tw_inv : smem;
+  const float2 *twf = Cfg::TG ? a.tw_fwd : smem + M;
+  float2 *const tw_end = Cfg::TG ? smem : smem + 2 * M;
+  float *red = reinterpret_cast<float *>(tw_end);
+  float2 *inter = tw_end + 32;              // after 64 floats of partials
   float2 *scratch_all = inter + (size_t)rows * W;
 
   const int tid = threadIdx.x;
@@ -201,7 +213,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         Dft<A, 1>::run(v);
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) {
-          const float2 w = twi[k1 * B + b];
+          const float2 w = tw_at<Cfg>(twi, k1 * B + b);
           scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], w);
         }
       }
@@ -307,7 +319,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           v[aa] = ((in_mask[u] >> aa) & 1u) ? col_base[aa * B * W + inter_swz(B * aa + b, c)] : make_float2(0.f, 0.f);
         Dft<A, 1>::run(v);
 #pragma unroll
-        for (int k1 = 0; k1 < A; ++k1) scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], twi[k1 * B + b]);
+        for (int k1 = 0; k1 < A; ++k1) scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], tw_at<Cfg>(twi, k1 * B + b));
       }
     }
     __syncwarp(gmask);
@@ -354,7 +366,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       if (k1 < A) {
 #pragma unroll
         for (int kk = 0; kk < B; ++kk)
-          scr[k1 * (B + 1) + kk] = (kk == 0) ? keep[u][0] : cmul(keep[u][kk], twf[kk * A + k1]);
+          scr[k1 * (B + 1) + kk] = (kk == 0) ? keep[u][0] : cmul(keep[u][kk], tw_at<Cfg>(twf, kk * A + k1));
       }
     }
     __syncwarp(gmask);
@@ -420,7 +432,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         }
         Dft<B, -1>::run(v);
 #pragma unroll
-        for (int kk = 0; kk < B; ++kk) scr[b2 * (B + 1) + kk] = (kk == 0) ? v[0] : cmul(v[kk], twf[kk * A + b2]);
+        for (int kk = 0; kk < B; ++kk) scr[b2 * (B + 1) + kk] = (kk == 0) ? v[0] : cmul(v[kk], tw_at<Cfg>(twf, kk * A + b2));
       }
     }
     __syncwarp(gmask);

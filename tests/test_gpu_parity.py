@@ -328,12 +328,15 @@ def test_update_kernel_variants_are_bit_identical(monkeypatch):
     for bit, whichever variant the autotuner picks."""
     j = job("m256_epry")
     outs = []
-    for t in (448, 384, 256, 192):                      # 192: four-CTA clusters, two CTAs per SM
-        monkeypatch.setenv("FPM_UPDATE_THREADS", str(t))
+    # threads per CTA x CTAs per cluster; the 4-CTA variants run two CTAs per SM,
+    # 256x4 with its twiddles read from global memory
+    for sel in ("448x2", "384x2", "256x2", "256x4", "192x4"):
+        monkeypatch.setenv("FPM_UPDATE_THREADS", sel)
         p = j.plan(iters=2)
         p.load_tiles(j.stack, j.counts_per_unit)
         p.reconstruct(2, mode="waves", graph=True)
-        assert p.stats()["run_threads"] == t
+        assert p.stats()["run_threads"] == int(sel.split("x")[0])
+        assert p.info["cluster"] == int(sel.split("x")[1])
         outs.append([p.spectrum(t_) for t_ in range(j.w.n_tiles)] + [p.pupil(t_) for t_ in range(j.w.n_tiles)])
         p.close()
     for o in outs[1:]:
