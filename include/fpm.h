@@ -298,6 +298,9 @@ typedef struct {
   double ms;         /* device time of `iters` loops on the plan's data          */
 } fpm_tune_entry;
 
+/* Most candidates fpm_autotune times; an `entries` array this long receives them all. */
+#define FPM_TUNE_MAX_ENTRIES 64
+
 /*
  * fpm_autotune -- time every execution path that fits the plan's tile side
  * (wave-by-wave launches with each update-kernel variant -- threads per CTA,
@@ -307,7 +310,8 @@ typedef struct {
  * loaded data, each replayed as a CUDA graph after a warm-up, and keep the
  * fastest for FPM_RUN_AUTO and for FPM_RUN_WAVES.  The plan's spectra and pupils
  * are saved first and restored afterwards.  entries (may be NULL) receives up
- * to max_entries results, *n_entries their count, *best the chosen index.
+ * to max_entries results, *n_entries their count, *best the chosen index
+ * (which may lie beyond max_entries when that is below FPM_TUNE_MAX_ENTRIES).
  * Synchronises the device.  FPM_ESTATE before fpm_load_tiles.
  */
 FPM_API int fpm_autotune(fpm_plan *plan, int32_t iters, void *stream, fpm_tune_entry *entries, int32_t max_entries,

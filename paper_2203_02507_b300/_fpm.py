@@ -27,6 +27,7 @@ RUN_GRAPH = 0x100
 RUN_TIMED = 0x200
 RUN_FAULT_TEST = 0x400
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+TUNE_MAX_ENTRIES = 64    # FPM_TUNE_MAX_ENTRIES
 
 
 class FpmError(RuntimeError):
@@ -232,9 +233,10 @@ class Plan:
         of the loaded data and keep the fastest (for mode="auto"); returns
         ([{mode, threads, cluster, ms}], best index)."""
         iters = self.info["iters"] if iters is None else iters
-        ent = (TuneEntry * 16)()
+        ent = (TuneEntry * TUNE_MAX_ENTRIES)()
         n, best = _i32(), _i32()
-        _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, 16, C.byref(n), C.byref(best)))
+        _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, TUNE_MAX_ENTRIES, C.byref(n),
+                                 C.byref(best)))
         names = {v: k for k, v in RUN.items()}
         out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "branches": e.branches, "ms": e.ms}
                for e in ent[:n.value]]

@@ -49,8 +49,12 @@ using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;
 using Cfg64w = UpdateCfg<64, 8, 8, 8, 1, 256, 2>;
 using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128, 2>;
 using Cfg128w = UpdateCfg<128, 16, 8, 8, 1, 256, 1>;
+using Cfg128o = UpdateCfg<128, 16, 8, 8, 2, 256, 2, 1, 0, 1>;
+using Cfg128t = UpdateCfg<128, 16, 8, 8, 2, 128, 3, 1, 1, 1>;
 using Cfg192 = UpdateCfg<192, 12, 16, 16, 1, 256, 1>;
 using Cfg192c = UpdateCfg<192, 12, 16, 16, 2, 256, 1>;
+using Cfg192h = UpdateCfg<192, 12, 16, 16, 2, 192, 2, 1, 1, 1>;
+using Cfg192o = UpdateCfg<192, 12, 16, 16, 4, 256, 2, 1, 0, 1>;
 using Cfg256 = UpdateCfg<256, 16, 16, 16, 2, 256, 1>;
 using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
@@ -58,10 +62,12 @@ using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2, 1, 1>;
 using Cfg256o = UpdateCfg<256, 16, 16, 16, 4, 256, 2, 1, 0, 1>;
 
 static const std::vector<Variant> &variants() {
-  static const std::vector<Variant> v = {make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg128>(),
-                                         make_variant<Cfg128w>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),
-                                         make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256o>(),
-                                         make_variant<Cfg256w>(), make_variant<Cfg256>()};
+  static const std::vector<Variant> v = {
+      make_variant<Cfg64>(),   make_variant<Cfg64w>(),                                                     // 64
+      make_variant<Cfg128o>(), make_variant<Cfg128t>(), make_variant<Cfg128>(),  make_variant<Cfg128w>(),  // 128
+      make_variant<Cfg192h>(), make_variant<Cfg192o>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),  // 192
+      make_variant<Cfg256o>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256w>(),
+      make_variant<Cfg256>()};                                                                          // 256
   return v;
 }
 

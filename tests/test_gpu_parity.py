@@ -322,15 +322,23 @@ def test_graph_branches_over_tile_groups_are_bit_identical(monkeypatch):
             assert np.array_equal(a, c)
 
 
-def test_update_kernel_variants_are_bit_identical(monkeypatch):
+# threads per CTA x CTAs per cluster of every update-kernel variant of a tile side
+VARIANTS = {
+    "m128_epry": ("128x1", "256x1", "256x2", "128x2"),
+    "m192_epry": ("256x1", "256x2", "192x2", "256x4"),
+    "m256_epry": ("256x4", "448x2", "384x2", "256x2", "192x4"),
+}
+
+
+@pytest.mark.parametrize("name", list(VARIANTS))
+def test_update_kernel_variants_are_bit_identical(name, monkeypatch):
     """Every update-kernel variant of a tile side (threads per CTA, CTAs per
-    cluster) runs the same per-row and per-column arithmetic: the same state bit
-    for bit, whichever variant the autotuner picks."""
-    j = job("m256_epry")
+    cluster, CTAs per SM, twiddles in shared or global memory, row prefetch)
+    runs the same per-row and per-column arithmetic: the same state bit for bit,
+    whichever variant the autotuner picks."""
+    j = job(name)
     outs = []
-    # threads per CTA x CTAs per cluster; the 4-CTA variants run two CTAs per SM,
-    # 256x4 with its twiddles read from global memory
-    for sel in ("448x2", "384x2", "256x2", "256x4", "192x4"):
+    for sel in VARIANTS[name]:
         monkeypatch.setenv("FPM_UPDATE_THREADS", sel)
         p = j.plan(iters=2)
         p.load_tiles(j.stack, j.counts_per_unit)
