@@ -34,23 +34,29 @@ import synth  # noqa: E402
 
 METRIC = "LED sub-aperture updates/sec and ms per FOV; p50/p99 job latency vs plain path"
 UNIT = "updates/s"
+E2E_IN_FLIGHT = 3      # FOVs in flight in the end-to-end measurement (plans on their own streams)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 148, 128, 2.032
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFLOP/s
 
-# DRAM bytes per update ((mode, m, threads per CTA) -> bytes) of the dominant
-# kernel, from the latest ncu capture in profiles/ of the kernel as it stands; a
-# launch scales it by the updates it processes.  Emptied whenever the kernel
-# changes until re-captured.
+# DRAM bytes per update ((mode, m, threads per CTA, CTAs per cluster) -> bytes)
+# of the dominant kernel, from the latest ncu capture in profiles/ of the kernel
+# as it stands; a launch scales it by the updates it processes.  Emptied
+# whenever the kernel changes until re-captured.
 TRAFFIC_PER_UPDATE = {
     # profiles/persistent_kernel_m256_ncu_full.md: 552,197,376 + 99,313,664 B for 3,600 updates
-    ("persistent", 256, 448): (552197376 + 99313664) / 3600,
+    ("persistent", 256, 448, 2): (552197376 + 99313664) / 3600,
     # profiles/update_kernel_m256_ncu_full.md: 12,489,984 + 0 B for 32 updates
-    ("waves", 256, 448): (12489984 + 0) / 32,
-    # profiles/update_kernel_m256_c4_ncu_full.md: 12,492,288 + 256 B for 32 updates
-    ("waves", 256, 192): (12492288 + 256) / 32,
+    ("waves", 256, 448, 2): (12489984 + 0) / 32,
+    # profiles/update_kernel_m256_4cta192_ncu_full.md: 12,492,288 + 256 B for 32 updates
+    ("waves", 256, 192, 4): (12492288 + 256) / 32,
+    # profiles/update_kernel_m256_4cta256_ncu_full.md: 12,491,264 + 256 B for 32 updates
+    ("waves", 256, 256, 4): (12491264 + 256) / 32,
 }
 
 EXTRA = {
+    # many small tiles: 16 x 16 tiles of 64 on a 1024^2 sensor, 15 x 15 LEDs, 10 loops, EPRY
+    "fov1024_m64": synth.Workload("fov1024_m64", sensor=1024, tile=64, tiles=16, overlap=0, iters=10, epry=True,
+                                  optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
     # small cases of the same kernels for ncu captures (inputs larger than L2, well under a few GB)
     "ncu_m256": synth.Workload("ncu_m256", sensor=768, tile=256, tiles=3, overlap=16, iters=1, epry=True,
                                optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
@@ -617,14 +623,15 @@ def main():
         kernel_timing = ("CUDA events around each update launch of one more step (one graph branch) run right "
                          "after the timed region; share = update time / (update + merge + load time) of that step, "
                          "the serialised kernel-time share an ncu launch list gives")
+    kkey = (args.mode, w.tile, st["run_threads"], st["run_cluster"])     # the kernel variant that ran
     achieved = fpu * upl / per_launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": (TRAFFIC_PER_UPDATE[(args.mode, w.tile, st["run_threads"])] * upl
-                        if (args.mode, w.tile, st["run_threads"]) in TRAFFIC_PER_UPDATE else None),
+            "traffic": (TRAFFIC_PER_UPDATE[kkey] * upl if kkey in TRAFFIC_PER_UPDATE else None),
             "traffic_source": "ncu dram__bytes_read+write per update on a 16-tile case (profiles/), "
                               "scaled by this launch's updates",
-            "kernel": kname, "launches_per_step": n_launch, "updates_per_launch": upl,
+            "kernel": kname, "kernel_variant": {"threads": st["run_threads"], "cluster": st["run_cluster"]},
+            "launches_per_step": n_launch, "updates_per_launch": upl,
             "avg_launch_us": per_launch_s * 1e6, "flop_per_update": fpu, "hbm_bytes_per_update": bpu,
             "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9, "kernel_share_of_step": share,
             "peak_source": "measured: fpm_fp32_peak (chains of FFMA on every FP32 lane, this device, this run)",
@@ -670,31 +677,52 @@ def main():
             plan.spectra(host_out[0])
             torch.cuda.synchronize()
         serial_s = (time.perf_counter() - t0) / k_e2e
-        # two FOVs in flight: two plans on two streams, so one FOV's copies overlap the other's compute
-        plan2 = plan_for(w)
-        plans, streams = [plan, plan2], [torch.cuda.Stream(), torch.cuda.Stream()]
+        # E2E_IN_FLIGHT FOVs in flight: as many plans on as many streams, so some FOVs' copies
+        # overlap the others' compute
+        extra = [plan_for(w) for _ in range(E2E_IN_FLIGHT - 1)]
+        plans = [plan] + extra
+        streams = [torch.cuda.Stream() for _ in plans]
+        while len(host_out) < len(plans):
+            host_out.append(torch.empty((w.n_tiles, w.hr, w.hr), dtype=torch.complex64, pin_memory=True))
+        # the other plans run the timed plan's kernel variant and branch count (read when their
+        # device state is made, at the first load)
+        env = {"FPM_WAVE_BRANCHES": str(line["config"]["graph_branches"])}
+        if tune:
+            best = tune["entries"][tune["best"]]
+            env["FPM_UPDATE_THREADS"] = f"{best['threads']}x{best['cluster']}"
+        prev_env = {key: os.environ.get(key) for key in env}
+        os.environ.update(env)
+        for q in extra:
+            q.load_tiles(stack, k)
+        for key, v in prev_env.items():
+            if v is None:
+                del os.environ[key]
+            else:
+                os.environ[key] = v
         torch.cuda.synchronize()
-        for j in range(2):
+        for j in range(len(plans)):
             plans[j].load_tiles(host_stack, k, stream=streams[j])
             plans[j].reconstruct(w.iters, mode=args.mode, graph=True, stream=streams[j])
             plans[j].spectra(host_out[j], stream=streams[j])
         torch.cuda.synchronize()
-        n_fov = 2 * k_e2e
+        n_fov = len(plans) * k_e2e
         t0 = time.perf_counter()
         for i in range(n_fov):
-            j = i % 2
+            j = i % len(plans)
             plans[j].load_tiles(host_stack, k, stream=streams[j])
             plans[j].reconstruct(w.iters, mode=args.mode, graph=True, stream=streams[j])
             plans[j].spectra(host_out[j], stream=streams[j])
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / n_fov
-        plan2.close()
+        for q in extra:
+            q.close()
         line["e2e"] = {"value": w.updates / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(host_stack.numel() * host_stack.element_size()),
                        "d2h_bytes_per_step": int(host_out[0].numel() * host_out[0].element_size()),
                        "ms_per_step": e2e_s * 1e3, "steps": n_fov,
-                       "how": "two plans on two streams, two FOVs in flight: every FOV's H2D, whole job and D2H "
-                              "in the timed region, copies overlapping the other FOV's compute",
+                       "how": f"{E2E_IN_FLIGHT} plans on {E2E_IN_FLIGHT} streams, {E2E_IN_FLIGHT} FOVs in flight: "
+                              "every FOV's H2D, whole job and D2H in the timed region, copies overlapping the "
+                              "other FOVs' compute",
                        "serial": {"value": w.updates / serial_s, "ms_per_step": serial_s * 1e3, "steps": k_e2e}}
         # plain path: one tile at a time, one LED per launch (bounded: one loop)
         plan.load_tiles(stack, k)

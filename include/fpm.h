@@ -279,7 +279,7 @@ typedef struct {
                                captured with; persistent: the persistent kernel's)     */
   int32_t online_launched;  /* wave steps the current or last online ingestion launched */
   int32_t online_steps;     /* wave steps of its schedule                               */
-  int32_t pad0;
+  int32_t run_cluster;      /* CTAs per cluster of that update kernel                   */
   double merge_ms;          /* device time between the end of each timed update launch
                                and the next launch's start (the wave's pupil merge)     */
 } fpm_stats;

@@ -73,7 +73,7 @@ class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
                 ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
                 ("persistent_clusters", C.c_int32), ("run_threads", C.c_int32), ("online_launched", C.c_int32),
-                ("online_steps", C.c_int32), ("pad0", C.c_int32), ("merge_ms", C.c_double)]
+                ("online_steps", C.c_int32), ("run_cluster", C.c_int32), ("merge_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -356,6 +356,7 @@ int make_queue(const std::vector<QueueJob> &jobs, QueueDev **out) {
 int queue_items(const QueueDev *q) { return q ? q->n_items : 0; }
 
 int persistent_block_threads(int m) { return m == 256 ? kPT256 : kPT; }
+int persistent_cluster_size(int) { return kPC; }
 
 int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, int *clusters_out) {
   if (q->n_items == 0) return FPM_OK;

@@ -37,6 +37,8 @@ int32_t schedule_steps(fpm_plan *p, int32_t iters);
 int queue_items(const QueueDev *q);
 // Threads per CTA of the persistent kernel for a queue whose jobs all have tile side m (0: mixed).
 int persistent_block_threads(int m);
+// CTAs per cluster of the persistent kernel for a queue whose jobs all have tile side m (0: mixed).
+int persistent_cluster_size(int m);
 // Reset the counters and `err` ([0] error bits, [1] abort flag) and launch the
 // persistent kernel on `st`.  stall_test > 0 makes every dependency wait look
 // at a flag nothing sets, with a 50 ms limit (exercises the timeout path).

@@ -47,6 +47,8 @@ static Variant make_variant() {
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
 using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;
 using Cfg64w = UpdateCfg<64, 8, 8, 8, 1, 256, 2>;
+using Cfg64c2 = UpdateCfg<64, 8, 8, 8, 2, 128, 4, 1, 1>;
+using Cfg64c4 = UpdateCfg<64, 8, 8, 8, 4, 128, 4, 1, 1>;
 using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128, 2>;
 using Cfg128w = UpdateCfg<128, 16, 8, 8, 1, 256, 1>;
 using Cfg128o = UpdateCfg<128, 16, 8, 8, 2, 256, 2, 1, 0, 1>;
@@ -63,7 +65,7 @@ using Cfg256o = UpdateCfg<256, 16, 16, 16, 4, 256, 2, 1, 0, 1>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {
-      make_variant<Cfg64>(),   make_variant<Cfg64w>(),                                                     // 64
+      make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg64c2>(), make_variant<Cfg64c4>(),  // 64
       make_variant<Cfg128o>(), make_variant<Cfg128t>(), make_variant<Cfg128>(),  make_variant<Cfg128w>(),  // 128
       make_variant<Cfg192h>(), make_variant<Cfg192o>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),  // 192
       make_variant<Cfg256o>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256w>(),
@@ -197,6 +199,8 @@ struct DeviceState {
   std::map<GraphKey, int64_t> graph_launches;
   std::map<GraphKey, int32_t> graph_threads;      // update-kernel threads captured in each graph
   int32_t run_threads = 0;                        // of the last fpm_reconstruct (fpm_get_stats)
+  int32_t run_cluster = 0;
+  std::map<GraphKey, int32_t> graph_cluster;      // its CTAs per cluster
   // counters (fpm_get_stats)
   int64_t load_launches = 0, run_launches = 0;
   std::vector<cudaEvent_t> events;            // 2 per wave step of a timed run
@@ -971,6 +975,7 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
   out->run_launches = d->run_launches;
   out->persistent_clusters = d->persistent_clusters;
   out->run_threads = d->run_threads;
+  out->run_cluster = d->run_cluster;
   online_progress(p, &out->online_launched, &out->online_steps);
   const int derr = device_error(p);
   out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
@@ -1155,6 +1160,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   fpm::DeviceState *d = p->dev;
   if (base == FPM_RUN_PERSISTENT) {
     d->run_threads = fpm::persistent_block_threads(p->m);
+    d->run_cluster = fpm::persistent_cluster_size(p->m);
     return fpm::run_persistent(p, iters, st, graph, stall);
   }
   if (!graph) {
@@ -1162,6 +1168,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     int rc = fpm::enqueue_reconstruct(p, iters, base, st, timed, false, &nl);
     d->run_launches = nl;
     d->run_threads = d->var->t;
+    d->run_cluster = d->var->c;
     return rc;
   }
   const int branches = (base == FPM_RUN_WAVES && !timed) ? std::min(d->branches, std::max(1, p->n_tiles)) : 1;
@@ -1184,6 +1191,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     else rc = fpm::enqueue_reconstruct(p, iters, base, cap, timed, true, &nl);
     d->graph_launches[key] = nl;
     d->graph_threads[key] = d->var->t;
+    d->graph_cluster[key] = d->var->c;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (own) cudaStreamDestroy(cap);
@@ -1214,6 +1222,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   FPM_CK(cudaGraphLaunch(it->second, st));
   d->run_launches = d->graph_launches[key];
   d->run_threads = d->graph_threads[key];
+  d->run_cluster = d->graph_cluster[key];
   return FPM_OK;
 }
 
@@ -1333,7 +1342,7 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
       const auto &c = cands[i];
       entries[i].mode = c.mode;
       entries[i].threads = c.v ? c.v->t : fpm::persistent_block_threads(p->m);
-      entries[i].cluster = c.v ? c.v->c : 2;
+      entries[i].cluster = c.v ? c.v->c : fpm::persistent_cluster_size(p->m);
       entries[i].branches = c.branches;
       entries[i].ms = c.ms;
     }

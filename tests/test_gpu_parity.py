@@ -324,6 +324,7 @@ def test_graph_branches_over_tile_groups_are_bit_identical(monkeypatch):
 
 # threads per CTA x CTAs per cluster of every update-kernel variant of a tile side
 VARIANTS = {
+    "m64_epry": ("128x1", "256x1", "128x2", "128x4"),
     "m128_epry": ("128x1", "256x1", "256x2", "128x2"),
     "m192_epry": ("256x1", "256x2", "192x2", "256x4"),
     "m256_epry": ("256x4", "448x2", "384x2", "256x2", "192x4"),
@@ -343,7 +344,8 @@ def test_update_kernel_variants_are_bit_identical(name, monkeypatch):
         p = j.plan(iters=2)
         p.load_tiles(j.stack, j.counts_per_unit)
         p.reconstruct(2, mode="waves", graph=True)
-        assert p.stats()["run_threads"] == int(sel.split("x")[0])
+        st = p.stats()
+        assert (st["run_threads"], st["run_cluster"]) == tuple(int(v) for v in sel.split("x"))
         assert p.info["cluster"] == int(sel.split("x")[1])
         outs.append([p.spectrum(t_) for t_ in range(j.w.n_tiles)] + [p.pupil(t_) for t_ in range(j.w.n_tiles)])
         p.close()
