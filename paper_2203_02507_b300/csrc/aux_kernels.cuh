@@ -107,6 +107,117 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
   }
 }
 
+// Lines of 256 (16 x 16) or 1024 (16 x 16 x 4) samples with the butterflies in
+// registers: the same Stockham passes, twiddles and radix order as
+// fft_lines_kernel (so the same results bit for bit), with compile-time
+// indices, the first pass fed straight from global memory and the last pass
+// stored straight to it where the lines are contiguous (elem_stride 1).  Lines
+// whose samples are strided (line_stride 1, elem_stride > 1) are staged through
+// shared memory G adjacent lines at a time, so every 32-byte sector is used
+// whole.  G lines per CTA, LEN / 16 threads per line; shared memory G *
+// line_padded_len(LEN) float2 (one buffer, a barrier between the reads and the
+// writes of each pass).
+template <int S, int LEN, int G>
+__global__ void __launch_bounds__(G *(LEN / 16)) fft_lines_reg_kernel(const __grid_constant__ FftLines f) {
+  static_assert(LEN == 256 || LEN == 1024, "lengths 16 x 16 and 16 x 16 x 4");
+  constexpr int NT = LEN / 16;                 // threads per line
+  constexpr int PL = line_padded_len(LEN);
+  extern __shared__ float2 line_buf[];
+  const int g = threadIdx.x / NT, t = threadIdx.x - g * NT;
+  const long long line0 = (long long)blockIdx.x * G;
+  const bool rows = f.elem_stride == 1;
+  // rows: each group's own line; strided: G adjacent lines of one batch
+  const long long line = rows ? line0 + g : line0;
+  const long long off = (line / f.lines_per_batch) * f.batch_stride + (line % f.lines_per_batch) * f.line_stride;
+  const int lb = (int)(line % f.lines_per_batch);     // index of the (first) line within its batch
+  const float2 *in = (f.src ? f.src : f.data) + off;
+  float2 *out = f.data + off;
+  float2 *xs = line_buf + (size_t)g * PL;
+  float2 v[16];
+  if (rows) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = in[t + r * NT];
+  } else {
+    for (int i = threadIdx.x; i < LEN * G; i += blockDim.x) {
+      const int e = i / G, c = i - e * G;
+      line_buf[(size_t)c * PL + line_pad(e)] = in[(long long)e * f.elem_stride + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = xs[line_pad(t + r * NT)];
+    __syncthreads();
+  }
+  // pass 1: radix 16, ns = 1 (no twiddles); butterfly t, outputs 16 t + r
+  Dft<16, S>::run(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) xs[line_pad(16 * t + r)] = v[r];
+  __syncthreads();
+  // pass 2: radix 16, ns = 16; butterfly t, inputs t + r NT, outputs (t / 16) 256 + t % 16 + 16 r
+  const int k2 = t % 16;
+  constexpr int step2 = LEN / 256;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    v[r] = xs[line_pad(t + r * NT)];
+    if (r > 0 && k2 > 0) v[r] = cmul(v[r], f.tw[k2 * r * step2]);
+  }
+  Dft<16, S>::run(v);
+  const int base2 = (t / 16) * 256 + k2;
+  // the finishing sign and scale of output sample e of line lb + c
+  auto finish = [&](float2 a, int e, int c) {
+    if (f.finish == 0.f) return a;
+    const float sc = ((e + lb + c) & 1) ? -f.finish : f.finish;
+    return make_float2(__fmul_rn(a.x, sc), __fmul_rn(a.y, sc));
+  };
+  if constexpr (LEN == 256) {
+    if (rows) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) out[base2 + 16 * r] = finish(v[r], base2 + 16 * r, 0);
+      return;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) xs[line_pad(base2 + 16 * r)] = v[r];
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) xs[line_pad(base2 + 16 * r)] = v[r];
+    __syncthreads();
+    // pass 3: radix 4, ns = 256; butterflies j = t + NT q, inputs j + 256 r, outputs j + 256 r
+    float2 w[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = t + NT * q;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        w[q][r] = xs[line_pad(j + 256 * r)];
+        if (r > 0 && j > 0) w[q][r] = cmul(w[q][r], f.tw[j * r]);
+      }
+      Dft<4, S>::run(w[q]);
+    }
+    if (rows) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = t + NT * q + 256 * r;
+          out[e] = finish(w[q][r], e, 0);
+        }
+      return;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) xs[line_pad(t + NT * q + 256 * r)] = w[q][r];
+  }
+  // strided lines: the G lines leave through shared memory, adjacent lines together
+  __syncthreads();
+  for (int i = threadIdx.x; i < LEN * G; i += blockDim.x) {
+    const int e = i / G, c = i - e * G;
+    out[(long long)e * f.elem_stride + c] = finish(line_buf[(size_t)c * PL + line_pad(e)], e, c);
+  }
+}
+
 // sqrt of each tile's image of the first LED, as a complex m x m array per tile.
 template <typename Img>
 __global__ void init_gather_kernel(float2 *out, const Img *stack, long long stride_led, long long stride_row,

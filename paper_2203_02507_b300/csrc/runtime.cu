@@ -333,6 +333,33 @@ int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int l
   f.elem_stride = elem_stride;
   f.lines_per_batch = lines_per_batch;
   f.finish = finish;
+  if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
+  // lengths 256 and 1024: butterflies in registers, G lines per CTA (rows: any lines;
+  // strided samples: G adjacent lines of one batch)
+  if (len == 256 || len == 1024) {
+    const int G = len == 256 ? 16 : 4;
+    const bool rows = elem_stride == 1;
+    const bool cols = line_stride == 1 && lines_per_batch % G == 0;
+    if ((rows || cols) && n_lines % G == 0) {
+      void (*kern)(FftLines);
+      if (len == 256) kern = sign > 0 ? &fft_lines_reg_kernel<1, 256, 16> : &fft_lines_reg_kernel<-1, 256, 16>;
+      else kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4> : &fft_lines_reg_kernel<-1, 1024, 4>;
+      const size_t smem = (size_t)G * line_padded_len(len) * sizeof(float2);
+      FPM_CK(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const long long max_chunk = (1LL << 30) / lines_per_batch * lines_per_batch;   // whole batches per launch
+      for (long long done = 0; done < n_lines;) {
+        const long long chunk = std::min<long long>(n_lines - done, max_chunk);
+        FftLines g = f;
+        const long long boff = (done / lines_per_batch) * batch_stride;
+        g.data = data + boff;
+        g.src = src ? src + boff : nullptr;
+        kern<<<(unsigned)(chunk / G), G * (len / 16), smem, st>>>(g);
+        done += chunk;
+      }
+      FPM_CK(cudaGetLastError());
+      return FPM_OK;
+    }
+  }
   // strided lines (columns): four adjacent ones per CTA, so loads and stores use whole sectors
   f.lines_per_cta = (line_stride == 1 && elem_stride > 1 && lines_per_batch % 4 == 0 && n_lines % 4 == 0) ? 4 : 1;
   if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
