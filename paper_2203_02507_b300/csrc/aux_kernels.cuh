@@ -118,7 +118,8 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
 // line_padded_len(LEN) float2 (one buffer, a barrier between the reads and the
 // writes of each pass).
 template <int S, int LEN, int G>
-__global__ void __launch_bounds__(G *(LEN / 16)) fft_lines_reg_kernel(const __grid_constant__ FftLines f) {
+__global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
+    fft_lines_reg_kernel(const __grid_constant__ FftLines f) {
   static_assert(LEN == 256 || LEN == 1024, "lengths 16 x 16 and 16 x 16 x 4");
   constexpr int NT = LEN / 16;                 // threads per line
   constexpr int PL = line_padded_len(LEN);
@@ -138,9 +139,17 @@ __global__ void __launch_bounds__(G *(LEN / 16)) fft_lines_reg_kernel(const __gr
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = in[t + r * NT];
   } else {
-    for (int i = threadIdx.x; i < LEN * G; i += blockDim.x) {
-      const int e = i / G, c = i - e * G;
-      line_buf[(size_t)c * PL + line_pad(e)] = in[(long long)e * f.elem_stride + c];
+    // 16 loads a thread, all in flight before their shared-memory stores
+    float2 u[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = threadIdx.x + q * G * NT, e = i / G, c = i - e * G;
+      u[q] = in[(long long)e * f.elem_stride + c];
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = threadIdx.x + q * G * NT, e = i / G, c = i - e * G;
+      line_buf[(size_t)c * PL + line_pad(e)] = u[q];
     }
     __syncthreads();
 #pragma unroll
@@ -212,8 +221,9 @@ __global__ void __launch_bounds__(G *(LEN / 16)) fft_lines_reg_kernel(const __gr
   }
   // strided lines: the G lines leave through shared memory, adjacent lines together
   __syncthreads();
-  for (int i = threadIdx.x; i < LEN * G; i += blockDim.x) {
-    const int e = i / G, c = i - e * G;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int i = threadIdx.x + q * G * NT, e = i / G, c = i - e * G;
     out[(long long)e * f.elem_stride + c] = finish(line_buf[(size_t)c * PL + line_pad(e)], e, c);
   }
 }

@@ -337,13 +337,15 @@ int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int l
   // lengths 256 and 1024: butterflies in registers, G lines per CTA (rows: any lines;
   // strided samples: G adjacent lines of one batch)
   if (len == 256 || len == 1024) {
-    const int G = len == 256 ? 16 : 4;
     const bool rows = elem_stride == 1;
+    // strided 1024-sample lines: 8 adjacent ones per CTA, 64-byte row segments
+    const int G = len == 256 ? 16 : rows ? 4 : 8;
     const bool cols = line_stride == 1 && lines_per_batch % G == 0;
     if ((rows || cols) && n_lines % G == 0) {
       void (*kern)(FftLines);
       if (len == 256) kern = sign > 0 ? &fft_lines_reg_kernel<1, 256, 16> : &fft_lines_reg_kernel<-1, 256, 16>;
-      else kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4> : &fft_lines_reg_kernel<-1, 1024, 4>;
+      else if (rows) kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4> : &fft_lines_reg_kernel<-1, 1024, 4>;
+      else kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 8> : &fft_lines_reg_kernel<-1, 1024, 8>;
       const size_t smem = (size_t)G * line_padded_len(len) * sizeof(float2);
       FPM_CK(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const long long max_chunk = (1LL << 30) / lines_per_batch * lines_per_batch;   // whole batches per launch

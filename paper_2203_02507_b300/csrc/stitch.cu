@@ -70,14 +70,17 @@ static __global__ void __launch_bounds__(kBandThreads) band_sums_kernel(const fl
   const int ya = y0 + rows * z / kBandChunks, yb = y0 + rows * (z + 1) / kBandChunks;
   const float2 *o = obj + (size_t)t * n * n;
   // a thread's few dozen samples in FP32 (FP64 arithmetic is slow on this part),
-  // the block's partials combined in FP64
+  // the block's partials combined in FP64; the threads stride over the chunk's
+  // samples row after row, so narrow column bands keep every thread busy
   float re = 0.f, im = 0.f;
-  for (int y = ya; y < yb; ++y)
-    for (int x = x0 + (int)threadIdx.x; x < x1; x += kBandThreads) {
-      const float2 v = o[(size_t)y * n + x];
-      re += v.x;
-      im += v.y;
-    }
+  const int width = x1 - x0, count = (yb - ya) * width;
+#pragma unroll 4
+  for (int i = (int)threadIdx.x; i < count; i += kBandThreads) {
+    const int y = ya + i / width, x = x0 + i % width;
+    const float2 v = o[(size_t)y * n + x];
+    re += v.x;
+    im += v.y;
+  }
   sre[threadIdx.x] = (double)re;
   sim[threadIdx.x] = (double)im;
   __syncthreads();
