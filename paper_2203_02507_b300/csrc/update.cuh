@@ -68,12 +68,21 @@ struct ImgCol {
 #pragma unroll
     for (int i = 0; i < WORDS; ++i) w[i] = 0u;
   }
+  // pixel k as a float: a 16-bit value u is placed in the mantissa of 2^23
+  // (one byte permute) and 2^23 subtracted, exact for every u < 2^23
   __device__ __forceinline__ float get(int k) const {
     if constexpr (sizeof(Img) == 2) {
-      return (float)((w[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+      const unsigned bits = __byte_perm(w[k >> 1], 0x4B000000u, (k & 1) ? 0x7632u : 0x7610u);
+      return __fadd_rn(__uint_as_float(bits), -8388608.0f);
     } else {
       return __uint_as_float(w[k]);
     }
+  }
+  // the measured intensity of pixel k: counts times 1/counts_per_unit, negative
+  // values clamped to zero (16-bit counts are never negative)
+  __device__ __forceinline__ float intensity(int k, float inv_counts) const {
+    if constexpr (sizeof(Img) == 2) return __fmul_rn(get(k), inv_counts);
+    else return fmaxf(__fmul_rn(get(k), inv_counts), 0.f);
   }
 };
 
@@ -334,26 +343,25 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         Dft<B, 1>::run(v);
         // amplitude step at y = k1 + A k2, without branches: sqrt(I) / |phi~| =
         // I / sqrt(I |phi~|^2), the hardware reciprocal square root refined by one
-        // Newton-Raphson step, r += r (1 - x r^2) / 2.  Pixels with phi~ = 0 (rare)
-        // are flagged and take sqrt(I) afterwards.
+        // Newton-Raphson step, r += r (1 - x r^2) / 2.  x is held at FLT_MIN or
+        // above, so I = 0 gives 0 * (finite r) = 0 with no select.  Pixels with
+        // phi~ = 0 (rare) are flagged and take sqrt(I) afterwards.
         unsigned zmask = 0;
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const float in = fmaxf(__fmul_rn(meas[u].get(k2), a.inv_counts), 0.f);
+          const float in = meas[u].intensity(k2, a.inv_counts);
           const float2 f = v[k2];
           const float m2 = cabs2(f);
-          const float x = __fmul_rn(in, m2);
+          const float x = fmaxf(__fmul_rn(in, m2), 1.17549435e-38f);
           float r = rsqrtf(x);
           r = __fmaf_rn(__fmul_rn(0.5f, r), __fmaf_rn(-__fmul_rn(x, r), r, 1.0f), r);
-          const float s = (in > 0.f) ? __fmul_rn(in, r) : 0.f;
-          const float2 scaled = cscale(f, s);
-          v[k2] = (m2 > 0.f) ? scaled : make_float2(0.f, 0.f);
+          v[k2] = cscale(f, __fmul_rn(in, r));
           zmask |= (m2 > 0.f) ? 0u : (1u << k2);
         }
         if (zmask) {
 #pragma unroll
           for (int k2 = 0; k2 < B; ++k2)
-            if ((zmask >> k2) & 1u) v[k2] = make_float2(sqrtf(fmaxf(__fmul_rn(meas[u].get(k2), a.inv_counts), 0.f)), 0.f);
+            if ((zmask >> k2) & 1u) v[k2] = make_float2(sqrtf(meas[u].intensity(k2, a.inv_counts)), 0.f);
         }
         // forward DFT, first pass of the B x A split: unit b' = k1, over a' = k2
         Dft<B, -1>::run(v);
