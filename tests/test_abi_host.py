@@ -104,3 +104,28 @@ def test_sequential_flag_gives_one_update_per_wave():
         assert list(s["waves"][t]) == list(range(2 * w.n_leds))
     assert p.info["max_wave_width"] == 1 and p.info["max_waves"] == 2 * w.n_leds
     p.close()
+
+
+@pytest.mark.parametrize("sel,tile,want", [
+    (None, 256, (256, 4)), (None, 192, (192, 2)), (None, 128, (256, 2)), (None, 64, (128, 1)),
+    ("448", 256, (448, 2)), ("448x2", 256, (448, 2)), ("256x2", 256, (256, 2)), ("192x4", 256, (192, 4)),
+    ("128x4", 64, (128, 4)), ("999", 256, (256, 4)),
+])
+def test_update_variant_selection(sel, tile, want, monkeypatch):
+    """The update-kernel variant a plan starts with (before any tuning): the first
+    of its tile side, or the one FPM_UPDATE_THREADS names by threads per CTA, or
+    threads x CTAs per cluster; a name that matches none falls back to the first."""
+    if sel is None:
+        monkeypatch.delenv("FPM_UPDATE_THREADS", raising=False)
+    else:
+        monkeypatch.setenv("FPM_UPDATE_THREADS", sel)
+    w = {64: synth.WORKLOADS["tile64_plain"], 128: synth.WORKLOADS["batch_m128"],
+         192: synth.WORKLOADS["batch_m192"], 256: synth.WORKLOADS["fov2048_m256"]}[tile]
+    p = fpm.plan_for(w, iters=1)
+    assert (p.info["threads"], p.info["cluster"]) == want
+    p.close()
+
+
+def test_tune_entry_limit_matches_the_header():
+    hdr = open(os.path.join(ROOT, "include", "fpm.h")).read()
+    assert int(re.search(r"#define FPM_TUNE_MAX_ENTRIES (\d+)", hdr).group(1)) == fpm.TUNE_MAX_ENTRIES
