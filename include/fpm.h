@@ -31,6 +31,13 @@
  *     thread-safe.
  *   - Device memory the library allocates belongs to the plan (or server) and is
  *     freed by fpm_plan_destroy (fpm_server_destroy).
+ *   - Environment overrides, read when a plan is created and when its device
+ *     state is made (its first load): FPM_UPDATE_THREADS = "T" or "TxC" picks the
+ *     update-kernel variant of the plan's tile side with T threads per CTA (and C
+ *     CTAs per cluster) instead of the default, which is the first that fits;
+ *     FPM_WAVE_BRANCHES = B (1..8) splits the tiles into B parallel graph branches
+ *     for graph replays of FPM_RUN_WAVES.  fpm_autotune replaces both with its
+ *     measured choice.
  */
 #ifndef FPM_H_
 #define FPM_H_
