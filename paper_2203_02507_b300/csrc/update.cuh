@@ -208,12 +208,14 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   for (int i = r0 + g; i < r1; i += G) {
     const int by = a.y_lo + i;
     // the group's next row into L2 while this one is worked on: lane l asks for
-    // the l-th 128-byte line of its spectrum and pupil rows (no registers held)
+    // the l-th 16-sample piece of its spectrum and pupil rows where it meets the
+    // support chord (no registers held)
     if (i + G < r1 && tl * 16 < M) {
-      const float2 *ns = spec + (size_t)(by + G) * n + tl * 16;
-      const float2 *np = pup + (size_t)(by + G) * M + tl * 16;
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(ns));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(np));
+      const int2 nc = a.chords[by + G];
+      if (tl * 16 + 15 >= nc.x && tl * 16 <= nc.y) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(spec + (size_t)(by + G) * n + tl * 16));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pup + (size_t)(by + G) * M + tl * 16));
+      }
     }
     if constexpr (!Cfg::PR) load_row(i);
 #pragma unroll
