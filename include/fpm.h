@@ -75,6 +75,11 @@ extern "C" {
                              corrected by all earlier ones (each wave holds one LED
                              per tile); default: wave-synchronous, LEDs whose
                              sub-apertures share no spectrum pixel in one wave   */
+#define FPM_EPRY_UNMASKED 4u /* with FPM_EPRY: the pupil correction is not confined
+                             to the circular support -- corrections, both
+                             normalisers and the wave footprints cover the whole
+                             m x m box (the initial pupil is still the circle);
+                             default: everything confined to the support disc     */
 
 /* ---- image element types --------------------------------------------------- */
 #define FPM_U16 0     /* camera counts (e.g. 12-bit)                             */
@@ -126,8 +131,9 @@ typedef struct {
 typedef struct {
   int32_t m, n;                 /* LR tile side, HR side                               */
   int32_t n_tiles, n_leds, iters;
-  int32_t support_px;           /* pixels of the circular pupil support (A)            */
-  int32_t support_rows;         /* rows of the support (R)                             */
+  int32_t support_px;           /* pixels where updates act: the circular pupil support
+                                   (A), m * m with FPM_EPRY_UNMASKED                   */
+  int32_t support_rows;         /* rows of that region (R)                             */
   int32_t max_waves;            /* largest wave count over the tiles                   */
   int32_t max_wave_width;       /* largest number of LEDs in one wave of one tile      */
   int64_t total_waves;          /* sum over tiles of their wave counts                 */
@@ -360,6 +366,8 @@ FPM_API int fpm_server_create(size_t hbm_budget_bytes, fpm_server **out);
  * The server runs the admitted jobs' wave steps together in rounds of one
  * persistent launch each, so jobs that arrive while others run join at the
  * next round; each job computes what fpm_reconstruct(plan, iters) computes.
+ * FPM_EINVAL for a plan whose update region the persistent kernel cannot hold
+ * (FPM_EPRY_UNMASKED at m = 256: run it with fpm_reconstruct instead).
  */
 FPM_API int fpm_submit(fpm_server *server, fpm_plan *plan, int32_t iters, const void *stack, int32_t dtype,
                        int32_t on_device, int64_t stride_led, int64_t stride_row, float counts_per_unit,

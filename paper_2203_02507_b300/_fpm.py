@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, EBUSY, ESTATE = 0, -1, -2, -3, -4,
 ORDER = {"center_out": 0, "raster": 1}
 EPRY = 1
 SEQUENTIAL = 2
+EPRY_UNMASKED = 4
 U16, F32 = 0, 1
 RUN = {"plain": 0, "waves": 1, "persistent": 2, "auto": 3}
 RUN_GRAPH = 0x100
@@ -163,7 +164,7 @@ class Plan:
 
     def __init__(self, *, sensor, tile, overlap, tiles, upsample, wavelength_um, na, pixel_um,
                  led_xy_um, led_height_um, defocus_um=None, order="center_out", iters=1, epry=False,
-                 sequential=False):
+                 sequential=False, unmasked=False):
         sh, sw = (sensor, sensor) if np.isscalar(sensor) else sensor
         ty, tx = (tiles, tiles) if np.isscalar(tiles) else tiles
         self._leds = np.ascontiguousarray(led_xy_um, dtype=np.float64).reshape(-1, 2)
@@ -180,7 +181,7 @@ class Plan:
                         if self._defocus is not None else None)
         d.order = ORDER[order]
         d.iters = int(iters)
-        d.flags = (EPRY if epry else 0) | (SEQUENTIAL if sequential else 0)
+        d.flags = (EPRY if epry else 0) | (SEQUENTIAL if sequential else 0) | (EPRY_UNMASKED if unmasked else 0)
         h = _vp()
         _check(_lib.fpm_plan_create(C.byref(d), C.byref(h)))
         self._h = h
@@ -396,7 +397,8 @@ def fp32_peak(stream=None) -> float:
     return v.value
 
 
-def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="center_out") -> Plan:
+def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="center_out",
+             unmasked=False) -> Plan:
     """Plan of a synth.Workload (square sensor and grid)."""
     from synth import led_grid, tile_defocus
     o = workload.optics
@@ -407,4 +409,4 @@ def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="cen
                 upsample=workload.upsample, wavelength_um=o.wavelength_um, na=o.na, pixel_um=o.pixel_um,
                 led_xy_um=led_grid(o.led_side, o.led_pitch_um), led_height_um=o.led_height_um,
                 defocus_um=defocus_um, iters=iters or workload.iters, epry=workload.epry, sequential=sequential,
-                order=order)
+                order=order, unmasked=unmasked)

@@ -40,6 +40,7 @@ struct fpm_plan {
   double wavelength_um = 0, na = 0, pixel_um = 0, led_height_um = 0, df = 0;
   bool epry = false;
   bool sequential = false;          // FPM_SEQUENTIAL: one update per wave
+  bool unmasked = false;            // FPM_EPRY_UNMASKED: updates over the whole m x m box
   std::vector<double> led_xy, defocus;
 
   // data-independent quantities (host, FP64 -> int / complex64)
@@ -48,7 +49,9 @@ struct fpm_plan {
   std::vector<int32_t> order;       // [L]
   std::vector<int32_t> waves;       // [T][iters * L]
   std::vector<int32_t> n_waves;     // [T]
-  std::vector<uint8_t> support;     // [m][m]
+  std::vector<uint8_t> support;     // [m][m] where updates act (the circular pupil support,
+                                    // or the whole box with FPM_EPRY_UNMASKED)
+  std::vector<uint8_t> circ;        // [m][m] the circular pupil support (initial pupils)
   std::vector<int32_t> chord_lo, chord_hi;   // [m], per box row; lo > hi when empty
   int32_t y_lo = 0, y_hi = -1;      // support rows (box coordinates)
   bool disc_ok = false;             // disc_half_width bounds every chord

@@ -356,6 +356,9 @@ int make_queue(const std::vector<QueueJob> &jobs, QueueDev **out) {
 int queue_items(const QueueDev *q) { return q ? q->n_items : 0; }
 
 int persistent_block_threads(int m) { return m == 256 ? kPT256 : kPT; }
+bool persistent_fits(int m, int rows) {
+  return std::max(persistent_smem(m, rows, m), persistent_smem(m, rows, 0)) <= 232448;
+}
 int persistent_cluster_size(int) { return kPC; }
 
 int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, int *clusters_out) {

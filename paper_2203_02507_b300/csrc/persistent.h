@@ -37,6 +37,9 @@ int32_t schedule_steps(fpm_plan *p, int32_t iters);
 int queue_items(const QueueDev *q);
 // Threads per CTA of the persistent kernel for a queue whose jobs all have tile side m (0: mixed).
 int persistent_block_threads(int m);
+// Whether tiles of side m with `rows` support rows fit the persistent kernel's shared
+// memory, in a queue of that side alone and in a mixed one.
+bool persistent_fits(int m, int rows);
 // CTAs per cluster of the persistent kernel for a queue whose jobs all have tile side m (0: mixed).
 int persistent_cluster_size(int m);
 // Reset the counters and `err` ([0] error bits, [1] abort flag) and launch the

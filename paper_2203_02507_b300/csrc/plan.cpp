@@ -108,6 +108,20 @@ static bool build_support(fpm_plan *p) {
                                p->chord_hi.data(), &p->y_lo, &p->y_hi);
   p->disc_ok = c > 0 && disc_bound_covers(p->m, p->y_lo, p->y_hi, p->chord_lo.data(), p->chord_hi.data());
   p->support_px = c > 0 ? c : 0;
+  p->circ = p->support;
+  if (c > 0 && p->unmasked) {
+    // unmasked EPRY: spectrum and pupil corrections, normalisers and footprints
+    // over the whole box; the initial pupil keeps the circular support
+    std::fill(p->support.begin(), p->support.end(), (uint8_t)1);
+    for (int by = 0; by < p->m; ++by) {
+      p->chord_lo[by] = 0;
+      p->chord_hi[by] = p->m - 1;
+    }
+    p->y_lo = 0;
+    p->y_hi = p->m - 1;
+    p->disc_ok = false;
+    p->support_px = p->m * p->m;
+  }
   return c > 0;
 }
 
@@ -121,7 +135,7 @@ static void build_pupils(fpm_plan *p) {
     for (int by = 0; by < m; ++by) {
       const double fy = (double)(by - m / 2) * p->df;
       for (int bx = 0; bx < m; ++bx) {
-        if (!p->support[(size_t)by * m + bx]) continue;
+        if (!p->circ[(size_t)by * m + bx]) continue;
         const double fx = (double)(bx - m / 2) * p->df;
         const double f2 = fx * fx + fy * fy;
         const double kz = std::sqrt(std::max(inv_l * inv_l - f2, 0.0)) - inv_l;
@@ -331,7 +345,9 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
   if (d->iters < 1 || d->iters > 10000) return fail(FPM_EINVAL, "iters %d out of range", d->iters);
   if (d->order != FPM_ORDER_CENTER_OUT && d->order != FPM_ORDER_RASTER)
     return fail(FPM_EINVAL, "unknown order %d", d->order);
-  if (d->flags & ~(FPM_EPRY | FPM_SEQUENTIAL)) return fail(FPM_EINVAL, "unknown flags 0x%x", d->flags);
+  if (d->flags & ~(FPM_EPRY | FPM_SEQUENTIAL | FPM_EPRY_UNMASKED)) return fail(FPM_EINVAL, "unknown flags 0x%x", d->flags);
+  if ((d->flags & FPM_EPRY_UNMASKED) && !(d->flags & FPM_EPRY))
+    return fail(FPM_EINVAL, "FPM_EPRY_UNMASKED needs FPM_EPRY");
 
   fpm_plan *p = new (std::nothrow) fpm_plan();
   if (!p) return fail(FPM_ENOMEM, "out of host memory");
@@ -353,6 +369,7 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
   p->led_height_um = d->led_height_um;
   p->epry = (d->flags & FPM_EPRY) != 0;
   p->sequential = (d->flags & FPM_SEQUENTIAL) != 0;
+  p->unmasked = (d->flags & FPM_EPRY_UNMASKED) != 0;
   p->df = 1.0 / (m * d->pixel_um);
   p->led_xy.assign(d->led_xy_um, d->led_xy_um + (size_t)d->n_leds * 2);
   for (double v : p->led_xy)

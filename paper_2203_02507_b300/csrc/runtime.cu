@@ -274,6 +274,7 @@ int ensure_device_state(fpm_plan *p) {
   d->var = find_variant(p->m, rows);
   if (!d->var) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", p->m, rows);
   if (const char *env = getenv("FPM_WAVE_BRANCHES")) d->branches = std::max(1, std::min(kMaxBranches, atoi(env)));
+  if (!persistent_fits(p->m, rows)) d->tuned_mode = FPM_RUN_WAVES;   // FPM_RUN_AUTO before any tuning
   const size_t T = p->n_tiles, n = p->n, m = p->m;
   cudaError_t e;
   for (const auto &v : variants())            // every fitting variant may be chosen by the autotuner
@@ -1303,7 +1304,7 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
       for (int b : {2, 4, 8})
         if (b <= p->n_tiles) cands.push_back({FPM_RUN_WAVES, &v, b, 0.0});
     }
-  cands.push_back({FPM_RUN_PERSISTENT, nullptr, 1, 0.0});
+  if (fpm::persistent_fits(p->m, rows)) cands.push_back({FPM_RUN_PERSISTENT, nullptr, 1, 0.0});
   const fpm::Variant *keep = d->var;
   const int32_t keep_branches = d->branches;
   int rc = FPM_OK;

@@ -196,6 +196,9 @@ int fpm_submit(fpm_server *s, fpm_plan *p, int32_t iters, const void *stack, int
   fpm::clear_error();
   if (!s || !p || !out) return fail(FPM_EINVAL, "fpm_submit: null argument");
   if (iters < 1 || iters > p->iters) return fail(FPM_EINVAL, "iters %d outside 1..%d", iters, p->iters);
+  if (!fpm::persistent_fits(p->m, p->y_hi - p->y_lo + 1))
+    return fail(FPM_EINVAL, "the server runs jobs in the persistent kernel, whose shared memory cannot hold tile %d "
+                "with %d update rows (FPM_EPRY_UNMASKED at m = 256)", p->m, p->y_hi - p->y_lo + 1);
   size_t bytes = 0;
   if (stack) {
     size_t sb = 0;

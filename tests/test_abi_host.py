@@ -129,3 +129,34 @@ def test_update_variant_selection(sel, tile, want, monkeypatch):
 def test_tune_entry_limit_matches_the_header():
     hdr = open(os.path.join(ROOT, "include", "fpm.h")).read()
     assert int(re.search(r"#define FPM_TUNE_MAX_ENTRIES (\d+)", hdr).group(1)) == fpm.TUNE_MAX_ENTRIES
+
+
+@pytest.mark.parametrize("name,iters,tiles", [("tile64_plain", 2, [0]), ("fov2048_m256", 1, [0, 63]),
+                                              ("batch_m128", 2, [9])])
+def test_unmasked_epry_plan_covers_the_box(name, iters, tiles):
+    """FPM_EPRY_UNMASKED: the update region, hence the wave footprints, is the
+    whole m x m box (bit-exact against the oracle's waves with an all-true
+    support); the initial pupil keeps the circular support."""
+    w = synth.WORKLOADS[name].replace(epry=True)
+    dz = synth.tile_defocus(w.n_tiles, *w.defocus_um, w.seed_offset)
+    p = fpm.plan_for(w, defocus_um=dz, iters=iters, unmasked=True)
+    m = w.tile
+    assert p.info["support_px"] == m * m and p.info["support_rows"] == m
+    g = _oracle_geometry(w, dz)
+    s = p.schedule()
+    seq = orc.sequence(g.order, iters)
+    box = np.ones((m, m), bool)
+    for t in tiles:
+        assert np.array_equal(s["waves"][t], orc.waves(g.n, box, g.shifts[t], seq)), f"tile {t}"
+        p0 = p.initial_pupil(t)
+        assert np.array_equal(p0 != 0, g.support)
+    masked = fpm.plan_for(w, defocus_um=dz, iters=iters)
+    assert p.info["max_waves"] > masked.info["max_waves"]          # larger footprints, more waves
+    p.close()
+    masked.close()
+
+
+def test_unmasked_flag_needs_epry():
+    with pytest.raises(fpm.FpmError) as e:
+        fpm.Plan(**_desc(unmasked=True))
+    assert e.value.code == fpm.EINVAL

@@ -129,3 +129,33 @@ def test_sequential_epry_differs_from_waves_when_leds_share_a_wave():
     b = orc.reconstruct_tile(imgs, g.shifts[0], g.order, g.support, g.pupils[0], g.n, 1, True,
                              mode="sequential", spectrum0=init)
     assert not np.array_equal(a[1], b[1])
+
+
+def test_unmasked_epry_normaliser_is_the_box_maximum():
+    """Unmasked EPRY (the update region is the whole m x m box): O holds N^2 a at
+    c+s+k0 inside the pupil disc and N^2 2a at c+s+k1 outside it, P = e^{i theta}
+    on the disc, I = 4|a|^2.  Only k0 is imaged, so phi' = 2 phi and D is
+    N^2 a e^{i theta} at k0 alone; max|O_box|^2 over the box is |N^2 2a|^2, four
+    times the disc's, so dP(k0) = e^{i theta} / 4 (e^{i theta} with the mask)."""
+    m, n = 16, 64
+    circ = orc.pupil_support(m, 1.0 / (m * DX), LAM, NA)           # radius ~4.9 px
+    box = np.ones((m, m), bool)
+    theta = 0.9
+    pup = np.where(circ, np.exp(1j * theta), 0)
+    s = np.array([2, -3])
+    k0, k1 = np.array([1, 2]), np.array([-8, -8])          # k1: a box corner, outside the disc
+    assert circ[m // 2 + k0[0], m // 2 + k0[1]] and not circ[m // 2 + k1[0], m // 2 + k1[1]]
+    a = 0.5 + 0.2j
+    base = np.zeros((n, n), np.complex128)
+    base[n // 2 + s[0] + k0[0], n // 2 + s[1] + k0[1]] = n * n * a
+    base[n // 2 + s[0] + k1[0], n // 2 + s[1] + k1[1]] = n * n * 2 * a
+    img = np.full((m, m), 4 * abs(a) ** 2)
+    for sup, scale in ((box, 0.25), (circ, 1.0)):
+        spec = base.copy()
+        dp = orc.update_one(spec, pup, sup, s, img)
+        exp_dp = np.zeros((m, m), np.complex128)
+        exp_dp[m // 2 + k0[0], m // 2 + k0[1]] = scale * np.exp(1j * theta)
+        np.testing.assert_allclose(dp, exp_dp, atol=1e-12)
+        ref = base.copy()
+        ref[n // 2 + s[0] + k0[0], n // 2 + s[1] + k0[1]] = 2 * n * n * a    # the spectrum update is the same
+        np.testing.assert_allclose(spec, ref, atol=1e-8 * n * n)
