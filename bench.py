@@ -316,6 +316,37 @@ def sequential_timing(torch, stack, k, w, steps=2):
     return out
 
 
+def unmasked_timing(torch, stack, k, w, steps=2):
+    """Non-masked EPRY (FPM_EPRY_UNMASKED: corrections and footprints over the whole
+    box) on the same FOV, the whole job per step, wave by wave with 8 graph branches
+    (the persistent kernel cannot hold the whole box at m = 256)."""
+    from paper_2203_02507_b300 import plan_for
+    prev = os.environ.get("FPM_WAVE_BRANCHES")
+    os.environ["FPM_WAVE_BRANCHES"] = "8"
+    p = plan_for(w, unmasked=True)
+    p.load_tiles(stack, k)
+    if prev is None:
+        del os.environ["FPM_WAVE_BRANCHES"]
+    else:
+        os.environ["FPM_WAVE_BRANCHES"] = prev
+    s = torch.cuda.current_stream()
+    out = {"waves_per_tile": p.info["max_waves"], "updates_per_step": w.updates, "mode": "waves+graph, 8 branches",
+           "threads": p.info["threads"], "cluster": p.info["cluster"]}
+    p.reconstruct(w.iters, mode="waves", graph=True)          # warm-up (graph capture)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        p.load_tiles(stack, k)
+        p.reconstruct(w.iters, mode="waves", graph=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out.update({"updates_per_s": w.updates / (ms / 1e3), "ms_per_step": ms})
+    p.close()
+    return out
+
+
 def online_timing(plan, torch, host_stack, k, w):
     """Online ingestion (Sec. 3.4): the FOV's images pushed one at a time from page-locked
     host memory in the LED order, as fast as the host issues them.  Per image: device
@@ -509,7 +540,7 @@ def main():
                     help="auto: fpm_autotune picks the fastest path on one loop of the data")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
     ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
-    ap.add_argument("--only", choices=["stitch", "online", "sequential"],
+    ap.add_argument("--only", choices=["stitch", "online", "sequential", "unmasked"],
                     help="time only this part on the workload (profiling aid) and print its JSON")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -536,6 +567,8 @@ def main():
             part = stitch_timing(plan, torch, dev, stack, k, w)
         elif args.only == "sequential":
             part = sequential_timing(torch, stack, k, w)
+        elif args.only == "unmasked":
+            part = unmasked_timing(torch, stack, k, w)
         else:
             host_stack = torch.empty(stack.shape, dtype=stack.dtype, pin_memory=True)
             host_stack.copy_(stack)
@@ -761,6 +794,7 @@ def main():
         line["online"] = online_timing(plan, torch, host_stack, k, w)
         del host_stack, host_out
         line["sequential_epry"] = sequential_timing(torch, stack, k, w)
+        line["unmasked_epry"] = unmasked_timing(torch, stack, k, w)
         line["stitch"] = stitch_timing(plan, torch, dev, stack, k, w)
         line["uneven_batch"] = uneven_batch(torch, dev)
         if args.serving_jobs > 0:
