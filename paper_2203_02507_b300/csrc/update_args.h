@@ -6,7 +6,7 @@
 namespace fpm {
 
 // Row chunks of the pupil merge (merge_kernel).
-constexpr int kNormParts = 8;
+constexpr int kNormParts = 4;
 
 // Image layout read by the update kernel (m = A * B, the kernel's split): for
 // tile t and LED l the m x m image is stored column after column, and within
