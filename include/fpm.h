@@ -140,7 +140,7 @@ typedef struct {
   int64_t device_bytes;         /* device memory of the state fpm_load_tiles allocates
                                    (spectra, pupils and initial pupils, corrections),
                                    tile images apart                                    */
-  int32_t cluster;              /* CTAs that share one update (1 or 2)                 */
+  int32_t cluster;              /* CTAs that share one update (1, 2 or 4)              */
   int32_t threads;              /* threads per CTA of the update kernel                */
   int64_t image_elems;          /* elements of the tile images fpm_load_tiles keeps
                                    (n_tiles * n_leds * m * m, each of the stack's type) */
@@ -407,9 +407,14 @@ FPM_API int fpm_server_destroy(fpm_server *server);
  * holds until the process exits; sizes needing more are rejected with
  * FPM_EINVAL.  All calls on a device share that array, so calls that overlap
  * on the GPU (other streams, unordered host threads) race; calls on one
- * stream are ordered.  The first call on each device looks up the array's
- * address (and sets the kernels' shared-memory limit), so make it before
- * any timing-critical loop.  Stream-ordered; the caller synchronises.
+ * stream are ordered.  Every pointer must be device memory of the current
+ * device (memory of another GPU, or host memory, gives FPM_EINVAL); the
+ * caller must pass tensors of exactly the stated sizes, which the C call
+ * cannot check.  The first call on each device (and the first after the
+ * device's context is re-created, e.g. by cudaDeviceReset) looks up the
+ * array's address with cudaGetSymbolAddress and sets the kernels'
+ * shared-memory limit, so make it before any timing-critical loop and before
+ * any stream capture.  Stream-ordered; the caller synchronises.
  */
 FPM_API int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, int32_t m, const float *image,
                                    int32_t shift_y, int32_t shift_x, double wavelength_um, double na,

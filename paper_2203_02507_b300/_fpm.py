@@ -382,9 +382,26 @@ def update_tile_static(spectrum, pupil, image, shift, wavelength_um, na, pixel_u
 
     spectrum: device complex64 [N, N]; pupil: device complex64 [m, m]; image:
     device float32 [m, m]; shift: (sy, sx).  Updates spectrum (and pupil if
-    epry) in place, stream-ordered.
+    epry) in place, stream-ordered.  The C call cannot see the tensors' sizes,
+    so they are checked here: every argument must be a contiguous CUDA tensor of
+    the stated type and square shape, all three on one device; ValueError
+    otherwise, before anything reaches the library.
     """
-    n, m = int(spectrum.shape[-1]), int(pupil.shape[-1])
+    for name, t, dt in (("spectrum", spectrum, "complex64"), ("pupil", pupil, "complex64"),
+                        ("image", image, "float32")):
+        if not hasattr(t, "is_cuda") or str(t.dtype) != f"torch.{dt}":
+            raise ValueError(f"{name} must be a torch {dt} tensor, got {getattr(t, 'dtype', type(t))}")
+        if t.dim() != 2 or t.shape[0] != t.shape[1]:
+            raise ValueError(f"{name} must be square [side, side], got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if not _is_device(t):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    n, m = int(spectrum.shape[0]), int(pupil.shape[0])
+    if tuple(image.shape) != (m, m):
+        raise ValueError(f"image must be [{m}, {m}] like the pupil, got {tuple(image.shape)}")
+    if not (spectrum.device == pupil.device == image.device):
+        raise ValueError("spectrum, pupil and image must be on one device")
     _check(_lib.fpm_update_tile_static(_ptr(spectrum), n, _ptr(pupil), m, _ptr(image), int(shift[0]),
                                        int(shift[1]), float(wavelength_um), float(na), float(pixel_um),
                                        1 if epry else 0, _stream(stream)))

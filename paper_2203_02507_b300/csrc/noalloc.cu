@@ -15,6 +15,7 @@
 // call's contents; every byte a call reads is first written by that same call
 // (nothing has to start at zero), and calls that overlap on the GPU (different
 // streams, or different host threads without ordering) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,35 +32,75 @@ constexpr size_t kStaticScratchBytes = size_t(1) << 20;
 
 static __device__ __align__(256) unsigned char g_fpm_static_scratch[kStaticScratchBytes];
 
-// Host side: the array's device address, looked up once per device.
+// Host side: the array's device address.  It is looked up (cudaGetSymbolAddress,
+// with the device current) on the first call made on a device, and again
+// whenever that device's current context is not the one the address was taken
+// in (after cudaDeviceReset a new primary context loads the module afresh, so
+// an address cached from the old context would dangle).  The context is named
+// by its process-unique id, read through the driver entry points the runtime
+// hands out, so the library links no driver library of its own.
 constexpr int kMaxDevices = 64;
 static std::mutex g_scratch_mu;
 static void *g_scratch_addr[kMaxDevices] = {};
+static unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-static int scratch_address(void **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(FPM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Process-unique id of the calling thread's current context; 0 if it cannot be read.
+static unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+static int scratch_address(int dev, void **out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(FPM_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  // cudaFree(0) makes the device's primary context current, so the id read next
+  // is the context the address below belongs to
+  cudaError_t e = cudaFree(nullptr);
+  if (e != cudaSuccess) return fail(FPM_ECUDA, "initialising device %d: %s", dev, cudaGetErrorString(e));
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_fpm_static_scratch);
     if (e != cudaSuccess || !p)
       return fail(FPM_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return FPM_OK;
 }
 
-static bool is_device_pointer(const void *p) {
+// True when p is device (or managed) memory of device `dev`, the device the
+// kernels of this call run on.  Memory of another GPU is refused: without peer
+// access the kernels could not reach it.
+static bool is_device_pointer(const void *p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -94,8 +135,14 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   if (oy < 0 || ox < 0 || oy + m > n || ox + m > n)
     return fail(FPM_EINVAL, "shift (%d, %d) moves the %d x %d box out of the %d x %d spectrum", shift_y, shift_x, m,
                 m, n, n);
-  if (!fpm::is_device_pointer(spectrum) || !fpm::is_device_pointer(pupil) || !fpm::is_device_pointer(image))
-    return fail(FPM_EINVAL, "spectrum, pupil and image must be device memory");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FPM_EINVAL, "spectrum, pupil and image must be device memory (no CUDA device)");
+  }
+  if (!fpm::is_device_pointer(spectrum, cur) || !fpm::is_device_pointer(pupil, cur) ||
+      !fpm::is_device_pointer(image, cur))
+    return fail(FPM_EINVAL, "spectrum, pupil and image must be device memory of the current device %d", cur);
 
   // support chords, FP64, exactly as the plan computes them
   int32_t lo[256], hi[256], y_lo = 0, y_hi = -1;
@@ -108,7 +155,7 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
     return fail(FPM_EINVAL, "pupil support (%d rows) too large for tile %d", rows, m);
 
   void *base = nullptr;
-  int rc = fpm::scratch_address(&base);
+  int rc = fpm::scratch_address(cur, &base);
   if (rc) return rc;
   unsigned char *dev = static_cast<unsigned char *>(base);
 

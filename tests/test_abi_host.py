@@ -160,3 +160,41 @@ def test_unmasked_flag_needs_epry():
     with pytest.raises(fpm.FpmError) as e:
         fpm.Plan(**_desc(unmasked=True))
     assert e.value.code == fpm.EINVAL
+
+
+def test_static_update_wrapper_rejects_wrong_tensors_before_the_call():
+    """The allocation-free update cannot see tensor sizes through the C ABI, so its
+    binding refuses a wrong type, shape or device before calling the library."""
+    torch = pytest.importorskip("torch")
+    m, n = 64, 256
+    spec = torch.zeros((n, n), dtype=torch.complex64)
+    pup = torch.zeros((m, m), dtype=torch.complex64)
+    img = torch.zeros((m, m), dtype=torch.float32)
+    bad = [
+        (pup.to(torch.float32), "pupil"),                                       # wrong dtype
+        (torch.zeros((n, n // 2), dtype=torch.complex64), "spectrum"),        # not square
+        (torch.zeros((m, m), dtype=torch.float64), "image"),                  # wrong dtype
+        (torch.zeros((m, m), dtype=torch.uint8), "image"),
+        (torch.zeros((m // 2, m // 2), dtype=torch.float32), "image"),        # not the pupil's size
+        (np.zeros((m, m), np.float32), "image"),                               # not a tensor
+    ]
+    for arg, which in bad:
+        args = {"spectrum": spec, "pupil": pup, "image": img}
+        args[which] = arg
+        with pytest.raises(ValueError):
+            fpm.update_tile_static(args["spectrum"], args["pupil"], args["image"], (0, 0), 0.532, 0.1, 1.625, True)
+    with pytest.raises(ValueError, match="CUDA"):                              # host tensors
+        fpm.update_tile_static(spec, pup, img, (0, 0), 0.532, 0.1, 1.625, True)
+
+
+def test_static_update_refuses_host_pointers():
+    """Through the C ABI itself: host memory is not device memory of the current
+    device, so the call returns FPM_EINVAL and launches nothing."""
+    m, n = 64, 256
+    spec = np.zeros((n, n), np.complex64)
+    pup = np.zeros((m, m), np.complex64)
+    img = np.zeros((m, m), np.float32)
+    rc = fpm._lib.fpm_update_tile_static(spec.ctypes.data, n, pup.ctypes.data, m, img.ctypes.data, 0, 0, 0.532,
+                                         0.1, 1.625, 1, None)
+    assert rc == fpm.EINVAL
+    assert "device memory" in fpm._lib.fpm_last_error().decode()
