@@ -125,3 +125,37 @@ def test_strided_device_pushes_equal_offline():
     for a, b in zip(state(p, w), ref):
         assert np.array_equal(a, b)
     p.close()
+
+
+@pytest.mark.parametrize("w", JOBS, ids=[w.name for w in JOBS])
+@pytest.mark.parametrize("how", ["in_order", "shuffled"])
+def test_online_matches_oracle(w, how):
+    """Online ingestion against the FP64 oracle itself (not only against the
+    library's offline path): every tile's spectrum and pupil after the job's loops,
+    images pushed in LED order or shuffled, within the parity bounds of the
+    offline tests (spectrum max(1e-5, 4 x float32 floor), pupil max(1e-4, 4 x
+    floor))."""
+    from oracle import fpm_oracle as orc
+    from tests import _fp32
+    from tests._jobs import rel_l2
+    j = job(w)
+    p = j.plan()
+    seq = list(p.schedule()["order"])
+    if how == "shuffled":
+        seq = list(np.random.default_rng(11).permutation(w.n_leds))
+    p.online_begin(w.iters, dtype="u16", counts_per_unit=j.counts_per_unit)
+    for led in seq:
+        p.online_push(int(led), j.stack[led])
+    p.online_finish()
+    bad = []
+    for t in range(w.n_tiles):
+        imgs = j.tile_images(t)
+        spec, pup = orc.reconstruct_tile(imgs, j.g.shifts[t], j.g.order, j.g.support, j.g.pupils[t], j.g.n,
+                                         w.iters, True)
+        fs, fp = _fp32.floor(imgs, j.g.shifts[t], j.g.order, j.g.support, j.g.pupils[t], j.g.n, w.iters, True,
+                             spec, pup)
+        es, ep = rel_l2(p.spectrum(t), spec), rel_l2(p.pupil(t), pup)
+        if es >= max(1e-5, 4.0 * fs) or ep >= max(1e-4, 4.0 * fp):
+            bad.append((t, es, fs, ep, fp))
+    p.close()
+    assert not bad, bad
