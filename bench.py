@@ -280,6 +280,42 @@ def aggregate(ms_local, updates_local, dist=None, device=None):
     return ms_local, updates_local, updates_local / (ms_local / 1e3)
 
 
+def shard_gather_and_stitch(plan, w, stack, k, by_rank, rank, world, dist, torch, stream):
+    """After a sharded run (Sec. 5): every rank sends its tiles' spectra and pupils
+    to rank 0 (point-to-point), which writes them into a plan of the whole grid
+    and stitches the field of view (Eq. 1).  Returns the timings on rank 0."""
+    from paper_2203_02507_b300 import plan_for, shard
+    first, count = by_rank[rank]
+    specs = np.zeros((count, w.hr, w.hr), np.complex64)
+    pups = np.zeros((count, w.tile, w.tile), np.complex64)
+    for i in range(count):
+        specs[i] = plan.spectrum(i)
+        pups[i] = plan.pupil(i)
+    t0 = time.perf_counter()
+    all_s = shard.gather_tiles(specs, first, w.n_tiles, by_rank, rank, dist)
+    all_p = shard.gather_tiles(pups, first, w.n_tiles, by_rank, rank, dist)
+    gather_s = time.perf_counter() - t0
+    if rank != 0:
+        return None
+    q = plan_for(w)
+    q.load_tiles(stack, k)
+    for t in range(w.n_tiles):
+        q.set_state(t, all_s[t], all_p[t])
+    fov = torch.empty((q.info["fov_h"], q.info["fov_w"]), dtype=torch.complex64, device=stack.device)
+    q.stitch(fov)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    q.stitch(fov)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    q.close()
+    return {"ranks": world, "tiles_by_rank": by_rank, "gather_s": gather_s,
+            "gather_bytes": int(w.n_tiles * (w.hr * w.hr + w.tile * w.tile) * 8),
+            "stitch_ms": e0.elapsed_time(e1),
+            "how": "tile states (spectrum + pupil) copied to the host and sent to rank 0 point to point "
+                   "after the timed steps; rank 0 writes them into a whole-grid plan and stitches"}
+
+
 # ---------------------------------------------------------------------------
 # batched and served forms
 # ---------------------------------------------------------------------------
@@ -540,6 +576,9 @@ def main():
                     help="auto: fpm_autotune picks the fastest path on one loop of the data")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain path and CPU baseline")
     ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving sample (0 to skip)")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one FOV's tiles over the ranks by cost (strong scaling, Sec. 5) and gather the "
+                         "tile states on rank 0 for stitching, instead of one FOV replica per rank")
     ap.add_argument("--only", choices=["stitch", "online", "sequential", "unmasked"],
                     help="time only this part on the workload (profiling aid) and print its JSON")
     args = ap.parse_args()
@@ -562,6 +601,19 @@ def main():
     plan = plan_for(w)
     stack, k = device_stack(plan, w, torch, dev)
     stream = torch.cuda.current_stream()
+    units_local = w.updates
+    shard_range = None
+    if args.shard:
+        # this rank's contiguous share of the FOV's tiles, balanced by m^2 L iters (all
+        # tiles cost the same here); the stack stays whole, each tile reads its window
+        from paper_2203_02507_b300 import shard
+        ranges = shard.job_ranges([(w.n_tiles, w.tile, w.n_leds, w.iters)], world)
+        shard_by_rank = [(rr[0][1], rr[0][2]) if rr else (0, 0) for rr in ranges]
+        shard_range = shard_by_rank[rank]
+        plan.close()
+        plan = plan_for(w, tile_first=shard_range[0], tile_count=max(shard_range[1], 1))
+        units_local = shard_range[1] * w.n_leds * w.iters
+        args.no_extras = True
     if args.only:
         if args.only == "stitch":
             part = stitch_timing(plan, torch, dev, stack, k, w)
@@ -635,7 +687,7 @@ def main():
         instr_ms = i0.elapsed_time(i1)
         load_ms = l0.elapsed_time(i0)
     st = plan.stats()
-    ms, _, value = aggregate(ms, w.updates * args.steps, dist if world > 1 else None, dev)
+    ms, _, value = aggregate(ms, units_local * args.steps, dist if world > 1 else None, dev)
     ms_per_step = ms / args.steps
     launches = (st_timed["load_launches"] + st_timed["run_launches"]) * args.steps
 
@@ -665,8 +717,8 @@ def main():
             "hbm_gbs_algorithmic": bpu * upl / per_launch_s / 1e9, "kernel_share_of_step": share,
             "peak_source": "measured: fpm_fp32_peak (chains of FFMA on every FP32 lane, this device, this run)",
             "peak_nominal": FP32_PEAK_TFLOPS, "kernel_timing": kernel_timing,
-            "job_achieved": fpu * w.updates / (run_ms / 1e3) / 1e12,
-            "job_frac": fpu * w.updates / (run_ms / 1e3) / 1e12 / peak,
+            "job_achieved": fpu * units_local / (run_ms / 1e3) / 1e12,
+            "job_frac": fpu * units_local / (run_ms / 1e3) / 1e12 / peak,
             "job_timing": "the job's algorithmic work over the timed steps' reconstruction time (CUDA events "
                           "around fpm_reconstruct; for wave launches with graph branches the kernels of "
                           "different tile groups overlap)"}
@@ -687,6 +739,11 @@ def main():
                            "how": "CUDA events around fpm_reconstruct in every timed step; load = the rest of "
                                   "the step (fpm_load_tiles: tile-image gather and initial guess)"}}
 
+    if args.shard:
+        line["scaling"] = "strong"
+        line["config"]["parallelism"] = f"{world} GPU(s), the FOV's {w.n_tiles} tiles split by cost"
+        line["shard"] = shard_gather_and_stitch(plan, w, stack, k, shard_by_rank, rank, world,
+                                                dist if world > 1 else None, torch, stream)
     if not args.no_extras and rank == 0:
         # e2e through the public API with host buffers: per FOV the H2D of its stack (page-locked),
         # the whole job, and the D2H of every spectrum

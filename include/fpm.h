@@ -125,6 +125,13 @@ typedef struct {
   int32_t order;                /* FPM_ORDER_*                                         */
   int32_t iters;                /* iteration loops the schedule is built for (>= 1)    */
   uint32_t flags;               /* FPM_EPRY | FPM_SEQUENTIAL, or 0                      */
+  int32_t tile_first;           /* tile subset (Sec. 5: sub-regions sent to different
+                                   GPUs): the plan holds tiles [tile_first, tile_first
+                                   + tile_count) of the grid in row-major order, with
+                                   the geometry they have in the whole grid; both 0 =
+                                   the whole grid.  Tile t of such a plan is grid tile
+                                   tile_first + t.  fpm_stitch needs the whole grid.  */
+  int32_t tile_count;
 } fpm_plan_desc;
 
 /* Sizes of a plan, for allocating the arrays the getters fill. */
@@ -146,7 +153,7 @@ typedef struct {
                                    (n_tiles * n_leds * m * m, each of the stack's type) */
   int32_t hr_overlap;           /* lines neighbouring tile objects share: overlap * (N/m) */
   int32_t fov_h, fov_w;         /* size of fpm_stitch's image: N + (tiles - 1)(N - hr_overlap) */
-  int32_t pad0;
+  int32_t tile_first;           /* grid index of the plan's tile 0 (0 for the whole grid) */
 } fpm_plan_info;
 
 /*

@@ -48,6 +48,7 @@ class PlanDesc(C.Structure):
         ("led_height_um", C.c_double),
         ("defocus_um", C.POINTER(C.c_double)),
         ("order", C.c_int32), ("iters", C.c_int32), ("flags", C.c_uint32),
+        ("tile_first", C.c_int32), ("tile_count", C.c_int32),
     ]
 
 
@@ -58,7 +59,7 @@ class PlanInfo(C.Structure):
         ("max_waves", C.c_int32), ("max_wave_width", C.c_int32), ("total_waves", C.c_int64),
         ("device_bytes", C.c_int64), ("cluster", C.c_int32), ("threads", C.c_int32),
         ("image_elems", C.c_int64), ("hr_overlap", C.c_int32), ("fov_h", C.c_int32), ("fov_w", C.c_int32),
-        ("pad0", C.c_int32),
+        ("tile_first", C.c_int32),
     ]
 
     def as_dict(self):
@@ -164,7 +165,7 @@ class Plan:
 
     def __init__(self, *, sensor, tile, overlap, tiles, upsample, wavelength_um, na, pixel_um,
                  led_xy_um, led_height_um, defocus_um=None, order="center_out", iters=1, epry=False,
-                 sequential=False, unmasked=False):
+                 sequential=False, unmasked=False, tile_first=0, tile_count=0):
         sh, sw = (sensor, sensor) if np.isscalar(sensor) else sensor
         ty, tx = (tiles, tiles) if np.isscalar(tiles) else tiles
         self._leds = np.ascontiguousarray(led_xy_um, dtype=np.float64).reshape(-1, 2)
@@ -182,6 +183,7 @@ class Plan:
         d.order = ORDER[order]
         d.iters = int(iters)
         d.flags = (EPRY if epry else 0) | (SEQUENTIAL if sequential else 0) | (EPRY_UNMASKED if unmasked else 0)
+        d.tile_first, d.tile_count = int(tile_first), int(tile_count)
         h = _vp()
         _check(_lib.fpm_plan_create(C.byref(d), C.byref(h)))
         self._h = h
@@ -191,6 +193,7 @@ class Plan:
         self.m, self.n = info.m, info.n
         self.n_tiles, self.n_leds, self.iters = info.n_tiles, info.n_leds, info.iters
         self.epry = bool(epry)
+        self.tile_first = info.tile_first
         self._stack_ref = None
 
     # -- host-only queries -------------------------------------------------
@@ -415,7 +418,7 @@ def fp32_peak(stream=None) -> float:
 
 
 def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="center_out",
-             unmasked=False) -> Plan:
+             unmasked=False, tile_first=0, tile_count=0) -> Plan:
     """Plan of a synth.Workload (square sensor and grid)."""
     from synth import led_grid, tile_defocus
     o = workload.optics
@@ -426,4 +429,4 @@ def plan_for(workload, defocus_um=None, iters=None, sequential=False, order="cen
                 upsample=workload.upsample, wavelength_um=o.wavelength_um, na=o.na, pixel_um=o.pixel_um,
                 led_xy_um=led_grid(o.led_side, o.led_pitch_um), led_height_um=o.led_height_um,
                 defocus_um=defocus_um, iters=iters or workload.iters, epry=workload.epry, sequential=sequential,
-                order=order, unmasked=unmasked)
+                order=order, unmasked=unmasked, tile_first=tile_first, tile_count=tile_count)

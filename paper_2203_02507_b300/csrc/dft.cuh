@@ -5,6 +5,12 @@
 // differently in different kernels: every kernel that inlines these helpers
 // computes bit-identical results.
 //
+// Complex additions and subtractions run as one packed FP32x2 instruction on
+// the (re, im) pair (add.rn.f32x2 / sub.rn.f32x2, sm_100 and later): the same
+// two IEEE operations in one issue slot.  Where a butterfly multiplies by +-i
+// the real and imaginary parts trade places, which a packed instruction
+// cannot express, so those outputs are written out with scalar operations.
+//
 // dft<R, S>(v) replaces v[0..R) by X[k] = sum_n v[n] exp(S * 2 pi i n k / R),
 // natural order in and out.  S = +1 is the inverse direction (no 1/R factor),
 // S = -1 the forward one.  Twiddles inside a DFT are exact constants of the
@@ -14,8 +20,23 @@
 
 namespace fpm {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+  return *reinterpret_cast<const float2 *>(&r);
+}
+// a + S i d and a - S i d, part by part (the +-i swaps the parts of d)
+template <int S>
+__device__ __forceinline__ float2 cadd_si(float2 a, float2 d) {
+  return S > 0 ? make_float2(__fsub_rn(a.x, d.y), __fadd_rn(a.y, d.x)) : make_float2(__fadd_rn(a.x, d.y), __fsub_rn(a.y, d.x));
+}
+template <int S>
+__device__ __forceinline__ float2 csub_si(float2 a, float2 d) {
+  return S > 0 ? make_float2(__fadd_rn(a.x, d.y), __fsub_rn(a.y, d.x)) : make_float2(__fsub_rn(a.x, d.y), __fadd_rn(a.y, d.x));
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
@@ -54,11 +75,11 @@ __device__ __forceinline__ void dft2(float2 &a, float2 &b) {
 template <int S>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
   const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  const float2 t2 = cadd(a1, a3), t3 = mul_si<S>(csub(a1, a3));
+  const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
   a0 = cadd(t0, t2);
   a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  a1 = cadd_si<S>(t1, d);     // t1 + S i d
+  a3 = csub_si<S>(t1, d);     // t1 - S i d
 }
 
 // X[k] = sum v[n] w^{nk}, w = exp(S 2 pi i / 3)
@@ -99,14 +120,13 @@ struct Dft<8, S> {
     dft4<S>(e0, e1, e2, e3);
     dft4<S>(o0, o1, o2, o3);
     o1 = mul_cs<S>(o1, FPM_R2, FPM_R2);
-    o2 = mul_si<S>(o2);
     o3 = mul_cs<S>(o3, -FPM_R2, FPM_R2);
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
     v[1] = cadd(e1, o1);
     v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2);
-    v[6] = csub(e2, o2);
+    v[2] = cadd_si<S>(e2, o2);  // e2 + S i o2
+    v[6] = csub_si<S>(e2, o2);
     v[3] = cadd(e3, o3);
     v[7] = csub(e3, o3);
   }

@@ -42,6 +42,11 @@ struct fpm_plan {
   bool sequential = false;          // FPM_SEQUENTIAL: one update per wave
   bool unmasked = false;            // FPM_EPRY_UNMASKED: updates over the whole m x m box
   std::vector<double> led_xy, defocus;
+  // tile subset (Sec. 5, sub-regions sent to different GPUs): this plan holds
+  // tiles [tile_first, tile_first + n_tiles) of the tiles_y x tiles_x grid
+  // (row-major); subset = false when it holds the whole grid
+  int32_t tile_first = 0;
+  bool subset = false;
 
   // data-independent quantities (host, FP64 -> int / complex64)
   std::vector<int32_t> origins;     // [T][2] (y0, x0)

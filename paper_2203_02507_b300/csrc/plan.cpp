@@ -346,6 +346,11 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
   if (d->order != FPM_ORDER_CENTER_OUT && d->order != FPM_ORDER_RASTER)
     return fail(FPM_EINVAL, "unknown order %d", d->order);
   if (d->flags & ~(FPM_EPRY | FPM_SEQUENTIAL | FPM_EPRY_UNMASKED)) return fail(FPM_EINVAL, "unknown flags 0x%x", d->flags);
+  const int64_t grid_tiles = (int64_t)d->tiles_y * d->tiles_x;
+  if (d->tile_first < 0 || d->tile_count < 0 || (int64_t)d->tile_first + d->tile_count > grid_tiles ||
+      (d->tile_count == 0 && d->tile_first != 0))
+    return fail(FPM_EINVAL, "tile subset [%d, %d + %d) outside the %lld tiles of the grid", d->tile_first,
+                d->tile_first, d->tile_count, (long long)grid_tiles);
   if ((d->flags & FPM_EPRY_UNMASKED) && !(d->flags & FPM_EPRY))
     return fail(FPM_EINVAL, "FPM_EPRY_UNMASKED needs FPM_EPRY");
 
@@ -395,6 +400,20 @@ int fpm_plan_create(const fpm_plan_desc *d, fpm_plan **out) {
     return fail(FPM_EINVAL, "pupil support (%d rows) too large for tile %d: NA*m*pixel/wavelength too big", rows, m);
   }
   fpm::build_geometry(p);
+  if (d->tile_count > 0 && d->tile_count < grid_tiles) {   // keep the subset's tiles only
+    const int f = d->tile_first, c = d->tile_count, L = p->n_leds;
+    p->origins.erase(p->origins.begin(), p->origins.begin() + (size_t)f * 2);
+    p->origins.resize((size_t)c * 2);
+    p->shifts.erase(p->shifts.begin(), p->shifts.begin() + (size_t)f * L * 2);
+    p->shifts.resize((size_t)c * L * 2);
+    if (!p->defocus.empty()) {
+      p->defocus.erase(p->defocus.begin(), p->defocus.begin() + f);
+      p->defocus.resize(c);
+    }
+    p->n_tiles = c;
+    p->tile_first = f;
+    p->subset = true;
+  }
   // every sub-aperture box must stay inside the N x N spectrum
   for (int t = 0; t < p->n_tiles; ++t)
     for (int l = 0; l < p->n_leds; ++l) {
@@ -442,6 +461,7 @@ int fpm_plan_get_info(const fpm_plan *p, fpm_plan_info *info) {
   info->hr_overlap = p->overlap * p->upsample;
   info->fov_h = (int32_t)(n + (p->tiles_y - 1) * (n - info->hr_overlap));
   info->fov_w = (int32_t)(n + (p->tiles_x - 1) * (n - info->hr_overlap));
+  info->tile_first = p->tile_first;
   return FPM_OK;
 }
 

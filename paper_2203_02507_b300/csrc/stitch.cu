@@ -255,6 +255,7 @@ int fpm_get_object(fpm_plan *p, int32_t tile, void *dst, int32_t on_device, void
 int fpm_stitch(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
   fpm::clear_error();
   if (!p || !dst) return fail(FPM_EINVAL, "fpm_stitch: null argument");
+  if (p->subset) return fail(FPM_EINVAL, "fpm_stitch needs a plan of the whole tile grid (this one holds a subset)");
   int rc = fpm::check_loaded(p);
   if (rc) return rc;
   const fpm::StitchGeom g = fpm::stitch_geom(p);

@@ -51,6 +51,8 @@ struct UpdateCfg2 {
   static_assert(32 % TPT == 0 && T % 32 == 0, "groups must not straddle warps");
   static_assert(W % 16 == 0, "inter rows are swizzled in groups of 16");
   static_assert(T <= 512, "the normaliser holds one partial per warp in 16 slots");
+  static_assert(W % A == 0, "a CTA's columns hold whole radix-A groups (owner and column known at compile time)");
+  static_assert(UB == 1, "one radix-A unit per lane in the row phases");
   // shared memory in bytes for R support rows: [partials][inter R x W][scratch]
   static size_t smem_bytes(int rows) {
     return 64 * sizeof(float) + (size_t)rows * W * sizeof(float2) + (size_t)G * SCR * sizeof(float4);
@@ -179,9 +181,10 @@ __device__ __forceinline__ void run_update2(const UpdateArgs &a, int4 item, floa
         DftP<B, 1>::run(v);
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const int x = k1 + A * k2;
-          const int owner = (C > 1) ? x / W : 0;
-          const int p = (C > 1) ? x - owner * W : x;
+          // x = k1 + A k2 with k1 < A and W a multiple of A: the owning CTA and the
+          // group of A columns are fixed by k2 alone
+          const int owner = (A * k2) / W;
+          const int p = k1 + (A * k2) % W;
           inter_of[owner][inter2_at(i0, by0, p, W)] = cp_first(v[k2]);
           if (has1) inter_of[owner][inter2_at(i1, by1, p, W)] = cp_second(v[k2]);
         }
@@ -387,6 +390,21 @@ __device__ __forceinline__ void run_update2(const UpdateArgs &a, int4 item, floa
     float2 *__restrict__ s1 = spec + (size_t)by1 * n;
     const float2 *__restrict__ p0 = pup + (size_t)by0 * M;
     const float2 *__restrict__ p1 = pup + (size_t)by1 * M;
+    // O_box_old and P of both rows at this lane's outputs x = kk + B k2, fetched
+    // before the transforms so that their latency overlaps them
+    cpair ov[Cfg::UA][A], pv[Cfg::UA][A];
+#pragma unroll
+    for (int u = 0; u < Cfg::UA; ++u) {
+      const int kk = tl + u * TPT;
+#pragma unroll
+      for (int k2 = 0; k2 < A; ++k2) {
+        const int x = kk + B * k2;
+        const bool in0 = kk < B && x >= ch0.x && x <= ch0.y, in1 = kk < B && x >= ch1.x && x <= ch1.y;
+        const float2 z = make_float2(0.f, 0.f);
+        ov[u][k2] = cp_join(in0 ? s0[x] : z, in1 ? s1[x] : z);
+        pv[u][k2] = cp_join(in0 ? p0[x] : z, in1 ? p1[x] : z);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < Cfg::UB; ++u) {
       const int b2 = tl + u * TPT;   // b' in [0, A)
@@ -394,9 +412,8 @@ __device__ __forceinline__ void run_update2(const UpdateArgs &a, int4 item, floa
         cpair v[B];
 #pragma unroll
         for (int aa = 0; aa < B; ++aa) {
-          const int x = A * aa + b2;
-          const int owner = (C > 1) ? x / W : 0;
-          const int p = (C > 1) ? x - owner * W : x;
+          const int owner = (A * aa) / W;          // x = A aa + b2, b2 < A
+          const int p = b2 + (A * aa) % W;
           const float2 f0 = inter_of[owner][inter2_at(i0, by0, p, W)];
           const float2 f1 = has1 ? inter_of[owner][inter2_at(i1, by1, p, W)] : make_float2(0.f, 0.f);
           v[aa] = cp_join(f0, f1);
@@ -421,9 +438,7 @@ __device__ __forceinline__ void run_update2(const UpdateArgs &a, int4 item, floa
           const int x = kk + B * k2;
           const bool in0 = x >= ch0.x && x <= ch0.y, in1 = x >= ch1.x && x <= ch1.y;
           if (in0 || in1) {
-            const float2 z = make_float2(0.f, 0.f);
-            const cpair o = cp_join(in0 ? s0[x] : z, in1 ? s1[x] : z);
-            const cpair p = cp_join(in0 ? p0[x] : z, in1 ? p1[x] : z);
+            const cpair o = ov[u][k2], p = pv[u][k2];
             const cpair phi = cpmul(o, p);
             const cpair d = cpsub(cpscale(v[k2], scale2), phi);
             const cpair pc = cpmulc(d, p);        // D * conj(P)

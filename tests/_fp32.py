@@ -58,3 +58,60 @@ def floor(images, shifts, order, support, pupil0, n, iters, epry, ref_spec, ref_
     rs = float(np.linalg.norm(s32 - ref_spec) / np.linalg.norm(ref_spec))
     rp = float(np.linalg.norm(p32 - ref_pup) / np.linalg.norm(ref_pup))
     return rs, rp
+
+
+# ---------------------------------------------------------------------------
+# Step-by-step attribution of the float32 floor
+# ---------------------------------------------------------------------------
+
+STEPS = ("prod", "ifft", "amp", "fft", "delta", "spec", "dp", "merge", "state")
+
+
+def _r(x, on):
+    """x rounded to complex64 (kept in complex128) when `on`."""
+    return x.astype(np.complex64).astype(np.complex128) if on else x
+
+
+def _update_mixed(spectrum, pupil_, support, shift, intensity, p_norm, f32):
+    n = spectrum.shape[0]
+    m = pupil_.shape[0]
+    y0, x0 = orc.crop_origin(n, m, shift)
+    old = spectrum[y0:y0 + m, x0:x0 + m].copy()
+    scale = (m / n) ** 2
+    big_phi = _r(old * pupil_, "prod" in f32)
+    if "ifft" in f32:
+        phi = np.fft.ifft2(np.fft.ifftshift(big_phi.astype(np.complex64))).astype(np.complex64).astype(np.complex128)
+    else:
+        phi = orc.ifft2c(big_phi)
+    phi = scale * phi
+    amp = np.sqrt(np.maximum(intensity, 0.0))
+    mag = np.abs(phi)
+    phi_new = _r(np.where(mag > 0.0, amp * phi / np.where(mag > 0.0, mag, 1.0), amp), "amp" in f32)
+    if "fft" in f32:
+        big_new = np.fft.fftshift(np.fft.fft2(phi_new.astype(np.complex64))).astype(np.complex64).astype(np.complex128)
+    else:
+        big_new = orc.fft2c(phi_new)
+    delta = _r(big_new / scale - big_phi, "delta" in f32)
+    spectrum[y0:y0 + m, x0:x0 + m] = _r(old + np.conj(pupil_) * delta / p_norm, "spec" in f32)
+    o_norm = np.max(np.abs(old[support]) ** 2)
+    if o_norm == 0.0:
+        return np.zeros_like(pupil_)
+    return _r(np.where(support, np.conj(old) * delta / o_norm, 0.0), "dp" in f32)
+
+
+def reconstruct_mixed(images, shifts, order, support, pupil0, n, iters, f32):
+    """The oracle's wave-synchronous EPRY with the steps named in `f32` (a subset of
+    STEPS) rounded to float32 and every other step in FP64: f32 = () is the oracle
+    itself, f32 = STEPS the float32 restatement above."""
+    seq = orc.sequence(order, iters)
+    w = orc.waves(n, support, shifts, seq)
+    spec = _r(orc.initial_spectrum(images[int(order[0])], n), "state" in f32)
+    p = _r(pupil0.astype(np.complex128), "state" in f32)
+    for wid in range(int(w.max()) + 1):
+        members = np.nonzero(w == wid)[0]
+        ps = p.copy()
+        pn = np.max(np.abs(ps[support]) ** 2)
+        dps = [_update_mixed(spec, ps, support, shifts[int(seq[j])], images[int(seq[j])], pn, f32) for j in members]
+        for dp in dps:
+            p = _r(p + dp, "merge" in f32)
+    return spec, p
