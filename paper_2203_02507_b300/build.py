@@ -22,7 +22,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
           f"-I{os.path.join(ROOT, 'include')}"]
 CUFLAGS = ARCH + COMMON + ["-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
 SOURCES = ["plan.cpp", "runtime.cu", "persistent.cu", "server.cu", "noalloc.cu", "calib.cu", "stitch.cu", "online.cu"]
-HEADERS = ["internal.h", "runtime.h", "dft.cuh", "update.cuh", "update2.cuh", "dft2.cuh", "aux_kernels.cuh", "update_args.h", "persistent.h", "tile_images.cuh"]
+HEADERS = ["internal.h", "runtime.h", "dft.cuh", "update.cuh", "aux_kernels.cuh", "update_args.h", "persistent.h", "tile_images.cuh"]
 
 
 def _newest_dep():

@@ -117,13 +117,11 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   if (m < 16 || m > 4096 || m % 16) return fail(FPM_EINVAL, "tile side %d out of range", m);
   if (n < 2 * m || n > 8 * m || n % m)
     return fail(FPM_EINVAL, "HR side %d must be 2..8 times the tile side %d", n, m);
-  // layout of the static array: [pupil correction m*m][tables][image in the kernel's column layout];
-  // tables: [packed twiddles 2 x m float4][chords][twiddles 2 x m float2][item][shifts, origin][merge entry]
+  // layout of the static array: [pupil correction m*m][tables][image in the kernel's column layout]
   const size_t dp_bytes = (size_t)m * m * sizeof(float2);
   const size_t blob_off = fpm::align256(dp_bytes);
   const size_t chords_b = (size_t)m * sizeof(int2), tw_b = (size_t)m * sizeof(float2);
-  const size_t tw2_b = (size_t)m * sizeof(float4);
-  const size_t blob_bytes = 2 * tw2_b + chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + sizeof(int2);
+  const size_t blob_bytes = chords_b + 2 * tw_b + sizeof(int4) + 2 * sizeof(int2) + sizeof(int2);
   const size_t img_off = fpm::align256(blob_off + blob_bytes);
   const size_t need = img_off + (size_t)m * m * sizeof(float);
   if (need > fpm::kStaticScratchBytes)
@@ -162,18 +160,14 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   unsigned char *dev = static_cast<unsigned char *>(base);
 
   // tables, built on the stack and copied with one stream-ordered copy
-  alignas(16) unsigned char blob[2 * 256 * 16 + 256 * 8 + 2 * 256 * 8 + 64];
+  alignas(16) unsigned char blob[256 * 8 + 2 * 256 * 8 + 64];
   unsigned char *w = blob;
-  float4 *twi2 = reinterpret_cast<float4 *>(w);
-  float4 *twf2 = twi2 + m;
-  w += 2 * tw2_b;
   int2 *ch = reinterpret_cast<int2 *>(w);
   for (int i = 0; i < m; ++i) ch[i] = make_int2(lo[i], hi[i]);
   w += chords_b;
   float2 *twi = reinterpret_cast<float2 *>(w);
   float2 *twf = twi + m;
   fpm::update_twiddles(m, fa, fb, twi, twf);
-  fpm::packed_twiddles(twi, twf, m, twi2, twf2);
   w += 2 * tw_b;
   int4 *item = reinterpret_cast<int4 *>(w);
   *item = make_int4(0, 0, 0, 0);         // tile 0, LED 0, slot 0
@@ -185,12 +179,10 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   cudaError_t e = cudaMemcpyAsync(dev + blob_off, blob, blob_bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(FPM_ECUDA, "copy of the update tables: %s", cudaGetErrorString(e));
 
-  const float4 *d_twi2 = reinterpret_cast<const float4 *>(dev + blob_off);
-  const float4 *d_twf2 = d_twi2 + m;
-  const int2 *d_chords = reinterpret_cast<const int2 *>(dev + blob_off + 2 * tw2_b);
-  const float2 *d_twi = reinterpret_cast<const float2 *>(dev + blob_off + 2 * tw2_b + chords_b);
+  const int2 *d_chords = reinterpret_cast<const int2 *>(dev + blob_off);
+  const float2 *d_twi = reinterpret_cast<const float2 *>(dev + blob_off + chords_b);
   const float2 *d_twf = d_twi + m;
-  const int4 *d_item = reinterpret_cast<const int4 *>(dev + blob_off + 2 * tw2_b + chords_b + 2 * tw_b);
+  const int4 *d_item = reinterpret_cast<const int4 *>(dev + blob_off + chords_b + 2 * tw_b);
   const int2 *d_sh = reinterpret_cast<const int2 *>(d_item + 1);
   const int2 *d_mg = d_sh + 2;
   float2 *d_dp = reinterpret_cast<float2 *>(dev);
@@ -216,8 +208,6 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   a.chords = d_chords;
   a.tw_inv = d_twi;
   a.tw_fwd = d_twf;
-  a.tw2_inv = d_twi2;
-  a.tw2_fwd = d_twf2;
   a.images = d_img;
   a.inv_counts = 1.f;
   a.scale = (float)((double)n / m * (double)n / m);

@@ -17,7 +17,6 @@
 #include "persistent.h"
 #include "runtime.h"
 #include "update.cuh"
-#include "update2.cuh"
 
 namespace fpm {
 
@@ -37,18 +36,12 @@ struct Variant {
   int m, a, b, tpt, c, t;
   UpdateKernel k_u16, k_f32;
   size_t (*smem)(int rows);
-  int packed;               // 1: two transforms per lane on FP32x2 instructions (update2.cuh)
 };
 
 template <class Cfg>
 static Variant make_variant() {
   return Variant{Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, &update_kernel<Cfg, uint16_t>,
-                 &update_kernel<Cfg, float>, &Cfg::smem_bytes, 0};
-}
-template <class Cfg>
-static Variant make_variant2() {
-  return Variant{Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, &update2_kernel<Cfg, uint16_t>,
-                 &update2_kernel<Cfg, float>, &Cfg::smem_bytes, 1};
+                 &update_kernel<Cfg, float>, &Cfg::smem_bytes};
 }
 
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
@@ -69,16 +62,14 @@ using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
 using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2, 1, 1>;
 using Cfg256o = UpdateCfg<256, 16, 16, 16, 4, 256, 2, 1, 0, 1>;
-// packed (FP32x2) variants: (m, A, B, lanes per transform pair, cluster, threads, min CTAs/SM)
-using Cfg256p = UpdateCfg2<256, 16, 16, 16, 4, 128, 2>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {
       make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg64c2>(), make_variant<Cfg64c4>(),  // 64
       make_variant<Cfg128o>(), make_variant<Cfg128t>(), make_variant<Cfg128>(),  make_variant<Cfg128w>(),  // 128
       make_variant<Cfg192h>(), make_variant<Cfg192o>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),  // 192
-      make_variant<Cfg256o>(), make_variant2<Cfg256p>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(),
-      make_variant<Cfg256w>(), make_variant<Cfg256>()};                                                 // 256
+      make_variant<Cfg256o>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256w>(),
+      make_variant<Cfg256>()};                                                                          // 256
   return v;
 }
 
@@ -134,13 +125,6 @@ void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd) {
       const double ang = -2.0 * M_PI * (double)(bb * k1) / m;
       fwd[k1 * a + bb] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-}
-
-void packed_twiddles(const float2 *inv, const float2 *fwd, int m, float4 *inv2, float4 *fwd2) {
-  for (int i = 0; i < m; ++i) {
-    inv2[i] = make_float4(inv[i].x, inv[i].x, inv[i].y, inv[i].y);
-    fwd2[i] = make_float4(fwd[i].x, fwd[i].x, fwd[i].y, fwd[i].y);
-  }
 }
 
 std::vector<float2> twiddles_line(int len, int sign) {
@@ -199,7 +183,6 @@ struct DeviceState {
   float2 *pup0 = nullptr;                           // initial pupils [T][m][m] (each load starts from them)
   int2 *shifts = nullptr, *origins = nullptr, *chords = nullptr;
   float2 *tw_inv = nullptr, *tw_fwd = nullptr;      // update kernel split
-  float4 *tw2_inv = nullptr, *tw2_fwd = nullptr;    // the same, packed (w.x, w.x, w.y, w.y)
   float2 *twl_fwd_m = nullptr;                      // line FFT tables
 
   unsigned *err = nullptr;
@@ -267,8 +250,7 @@ void destroy_device_state(fpm_plan *p) {
     dfree(s.merges);
   }
   for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->pup0, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
-                  (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->tw2_inv,
-                  (void *)d->tw2_fwd, (void *)d->twl_fwd_m, (void *)d->err,
+                  (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
                   d->images, d->scratch})
     dfree(q);
   if (cur >= 0) cudaSetDevice(cur);
@@ -328,10 +310,6 @@ int ensure_device_state(fpm_plan *p) {
   update_twiddles(p->m, d->var->a, d->var->b, ti.data(), tf.data());
   if ((rc = upload(&d->tw_inv, ti.data(), ti.size() * sizeof(float2)))) return rc;
   if ((rc = upload(&d->tw_fwd, tf.data(), tf.size() * sizeof(float2)))) return rc;
-  std::vector<float4> ti2(p->m), tf2(p->m);
-  packed_twiddles(ti.data(), tf.data(), p->m, ti2.data(), tf2.data());
-  if ((rc = upload(&d->tw2_inv, ti2.data(), ti2.size() * sizeof(float4)))) return rc;
-  if ((rc = upload(&d->tw2_fwd, tf2.data(), tf2.size() * sizeof(float4)))) return rc;
   std::vector<float2> tl = twiddles_line(p->m, -1);
   if ((rc = upload(&d->twl_fwd_m, tl.data(), tl.size() * sizeof(float2)))) return rc;
   FPM_CK(cudaMalloc((void **)&d->err, 4 * sizeof(unsigned)));
@@ -482,8 +460,6 @@ static UpdateArgs make_args(fpm_plan *p, const StepDev *sd) {
   a.chords = d->chords;
   a.tw_inv = d->tw_inv;
   a.tw_fwd = d->tw_fwd;
-  a.tw2_inv = d->tw2_inv;
-  a.tw2_fwd = d->tw2_fwd;
   a.images = d->images;
   a.inv_counts = d->inv_counts;
   a.scale = (float)((double)p->n / p->m * (double)p->n / p->m);

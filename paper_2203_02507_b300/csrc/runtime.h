@@ -31,8 +31,6 @@ int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool
 bool update_variant(int m, int rows, int *a, int *b, int *cluster, int *threads);
 // Twiddle tables of the update kernel's two-pass split m = a * b (m entries each).
 void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd);
-// the same tables packed for the FP32x2 kernel: entry i = (w.x, w.x, w.y, w.y)
-void packed_twiddles(const float2 *inv, const float2 *fwd, int m, float4 *inv2, float4 *fwd2);
 // Launch the update kernel over items [item0, item0 + count) (image dtype FPM_U16 or FPM_F32).
 int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
                         cudaStream_t st);

@@ -45,8 +45,6 @@ struct UpdateArgs {
   const int2 *chords;         // [m] (lo, hi) support columns per box row
   const float2 *tw_inv;       // [m] exp(+2 pi i b k1/m) at k1*B + b
   const float2 *tw_fwd;       // [m] exp(-2 pi i b k1/m) at k1*A + b (the B x A split)
-  const float4 *tw2_inv;      // [m] the same twiddles as (w.x, w.x, w.y, w.y), for the packed kernel
-  const float4 *tw2_fwd;
   const void *images;         // [T][L][m][m] tile images in the column layout below
   float inv_counts;           // intensity = element * inv_counts
   float scale;                // (N/m)^2

@@ -30,9 +30,13 @@ to 2.5).  The 21 x 21-LED job is the extreme case: most of its LEDs are dark
 field and its float32 floor after 20 loops is 9e-2..2.7e-1 in amplitude, i.e.
 float32 and FP64 runs of the same algorithm are different iterates there.
 Since the divergence is between iterates, the reconstruction itself is judged
-too: over the sampled tiles of a job, the mean distance of the recovered object
-amplitude to the ground-truth object's must not exceed that of the CPU runs
-(for each tile the worse of the FP64 and complex64 runs) by more than 5%.
+too, one-sidedly: over the sampled tiles of a job, the mean distance of the
+recovered object amplitude to the ground-truth object's may exceed the CPU
+runs' mean (FP64 and complex64 averaged) by at most 5% or twice the mean gap
+between those two CPU runs, whichever is larger -- the GPU run must be no worse
+than another float32 run could be.  (On the headline the three runs agree
+within 2%; on the 21 x 21-LED job FP64 and complex64 runs differ by up to 37%
+on one tile.)
 """
 import numpy as np
 import pytest
@@ -46,7 +50,7 @@ from tests.test_gpu_fullsize import _stack_with_samples
 pytestmark = pytest.mark.gpu
 AMP_TOL, PHASE_TOL, PUPIL_TOL = 1e-3, 1e-3, 1e-3
 FLOOR_FACTOR = 4.0
-TRUTH_SLACK = 1.05
+TRUTH_SLACK = 0.05
 
 SMALL64 = synth.Workload("m64_15x15_full", sensor=256, tile=64, tiles=4, overlap=16, iters=20, epry=True,
                          optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0), seed_offset=5100)
@@ -124,11 +128,13 @@ def test_full_run_matches_oracle(name, mode, monkeypatch):
         fp = rel_l2(pup32, pup_ref)
         tg, to, t32 = _truth_error(spec, w, t), _truth_error(spec_ref, w, t), _truth_error(spec32, w, t)
         tg_all.append(tg)
-        tc_all.append(max(to, t32))
+        tc_all.append((to, t32))
         print(f"{name} {mode} tile {t}: amplitude {amp:.2e} (floor {famp:.2e}) phase {ph:.2e} (floor {fph:.2e}) "
               f"pupil {ep:.2e} (floor {fp:.2e}); vs ground truth GPU {tg:.4e} FP64 {to:.4e} complex64 {t32:.4e}")
         if not (amp <= max(AMP_TOL, FLOOR_FACTOR * famp) and ph <= max(PHASE_TOL, FLOOR_FACTOR * fph)
                 and ep <= max(PUPIL_TOL, FLOOR_FACTOR * fp)):
             bad.append((t, amp, famp, ph, fph, ep, fp))
     assert not bad, bad
-    assert np.mean(tg_all) <= TRUTH_SLACK * np.mean(tc_all), (tg_all, tc_all)
+    cpu = np.array(tc_all)
+    cpu_mean, cpu_gap = float(cpu.mean()), float(np.abs(cpu[:, 0] - cpu[:, 1]).mean())
+    assert np.mean(tg_all) <= cpu_mean + max(TRUTH_SLACK * cpu_mean, 2.0 * cpu_gap), (tg_all, tc_all)

@@ -327,7 +327,7 @@ VARIANTS = {
     "m64_epry": ("128x1", "256x1", "128x2", "128x4"),
     "m128_epry": ("128x1", "256x1", "256x2", "128x2"),
     "m192_epry": ("256x1", "256x2", "192x2", "256x4"),
-    "m256_epry": ("256x4", "128x4", "448x2", "384x2", "256x2", "192x4"),
+    "m256_epry": ("256x4", "448x2", "384x2", "256x2", "192x4"),
 }
 
 
