@@ -493,6 +493,56 @@ def uneven_batch(torch, dev, steps=3):
     return out
 
 
+def config_extra(name, torch, dev, peak, steps=2, tune_iters=2):
+    """Another configuration of the benchmark set, measured like the headline: the
+    path the autotuner picks on `tune_iters` loops of the job's own data, then the
+    whole job (load + initial guess + all loops) timed with CUDA events, and the
+    update kernel's per-launch roofline from one more, per-launch-timed step."""
+    from paper_2203_02507_b300 import plan_for
+    w = synth.WORKLOADS[name]
+    plan = plan_for(w)
+    stack, k = device_stack(plan, w, torch, dev, fast=w.n_tiles > 64)
+    plan.load_tiles(stack, k)
+    entries, best = plan.autotune(iters=tune_iters)
+    mode = entries[best]["mode"]
+
+    def step():
+        plan.load_tiles(stack, k)
+        plan.reconstruct(w.iters, mode=mode, graph=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert plan.stats()["device_error"] == 0
+    out = {"value": w.updates / (ms / 1e3), "unit": UNIT, "ms_per_job": ms, "steps": steps,
+           "updates_per_job": w.updates, "mode": mode + "+graph", "tuned": entries[best],
+           "config": {"sensor": w.sensor, "tile": w.tile, "tiles": w.n_tiles, "leds": w.n_leds, "iters": w.iters,
+                      "epry": w.epry, "image": w.image_dtype}}
+    # per-launch roofline of the update kernel (wave launches of the tuned variant, one branch)
+    plan.load_tiles(stack, k)
+    plan.reconstruct(w.iters, mode="waves", graph=True, timed=True)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    t_l = st["update_ms"] / 1e3 / st["update_launches"]
+    u_l = st["updates"] / st["update_launches"]
+    fpu = flops_per_update(w)
+    out["roofline"] = {"bound": "alu", "achieved": fpu * u_l / t_l / 1e12, "peak": peak, "unit": "TFLOP/s",
+                       "frac": fpu * u_l / t_l / 1e12 / peak, "avg_launch_us": t_l * 1e6,
+                       "updates_per_launch": u_l, "flop_per_update": fpu,
+                       "kernel_variant": {"threads": st["run_threads"], "cluster": st["run_cluster"]},
+                       "job_frac": fpu * w.updates / (ms / 1e3) / 1e12 / peak}
+    plan.close()
+    del stack
+    torch.cuda.synchronize()
+    return out
+
+
 def plain_rate(torch, dev, w):
     """Updates/s of the plain path (one tile at a time, one LED per launch) on one loop of `w`."""
     from paper_2203_02507_b300 import plan_for
@@ -538,6 +588,19 @@ def serving(torch, dev, n_jobs, budget=120 << 30):
     assert all(s[0] == "done" for s in states), states
     lat = np.array([s[2] for s in states])
     upd = sum(w.updates for _, w, _, _, _ in prepared)
+    # throughput: completed updates over the time the server had admitted work on
+    # the GPU (union of every job's admit -> done interval)
+    spans = sorted((arrival + s[1], arrival + s[2]) for (arrival, *_), s in zip(prepared, states))
+    busy, cur0, cur1 = 0.0, None, None
+    for a0, a1 in spans:
+        if cur1 is None or a0 > cur1:
+            if cur1 is not None:
+                busy += cur1 - cur0
+            cur0, cur1 = a0, a1
+        else:
+            cur1 = max(cur1, a1)
+    if cur1 is not None:
+        busy += cur1 - cur0
     # plain path, same arrivals: one job at a time (FIFO), each at the plain rate measured for its tile size
     rates = {}
     for m in sorted({w.tile for _, w, _, _, _ in prepared}):
@@ -553,7 +616,10 @@ def serving(torch, dev, n_jobs, budget=120 << 30):
     plain_lat = np.array(plain_lat)
     return {"jobs": n_jobs, "arrivals": "Poisson 2 jobs/s (first jobs of the 500-job stream)",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "updates_per_s": upd / t_end, "updates": upd, "wall_s": t_end,
+            "mean_s": float(lat.mean()), "updates_per_s": upd / busy, "updates": upd, "wall_s": t_end,
+            "busy_s": busy, "offered_updates_per_s": upd / t_end,
+            "throughput_how": "completed updates / GPU-busy time (union of the jobs' admit -> done intervals); "
+                              "offered_updates_per_s = updates / wall time of the arrival stream",
             "plain_path_model": {"p50_s": float(np.percentile(plain_lat, 50)),
                                  "p99_s": float(np.percentile(plain_lat, 99)),
                                  "plain_updates_per_s_by_tile": {str(k): v for k, v in rates.items()},
@@ -854,6 +920,8 @@ def main():
         line["unmasked_epry"] = unmasked_timing(torch, stack, k, w)
         line["stitch"] = stitch_timing(plan, torch, dev, stack, k, w)
         line["uneven_batch"] = uneven_batch(torch, dev)
+        for extra_name in ("tile64_plain", "fov5120_m128"):
+            line[extra_name] = config_extra(extra_name, torch, dev, peak)
         if args.serving_jobs > 0:
             line["serving"] = serving(torch, dev, args.serving_jobs)
         if world == 1:

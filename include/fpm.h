@@ -302,6 +302,9 @@ typedef struct {
   int32_t run_cluster;      /* CTAs per cluster of that update kernel                   */
   double merge_ms;          /* device time between the end of each timed update launch
                                and the next launch's start (the wave's pupil merge)     */
+  int32_t run_lanes;        /* lanes per 1-D transform (threads per transform) of that
+                               update kernel                                           */
+  int32_t pad0;
 } fpm_stats;
 
 /* fpm_get_stats -- fill *out.  Synchronises the device; update_ms is 0 when no
@@ -316,6 +319,10 @@ typedef struct {
   int32_t cluster;   /* CTAs per update                                          */
   int32_t branches;  /* wave launches: parallel graph branches over tile groups  */
   double ms;         /* device time of `iters` loops on the plan's data          */
+  int32_t lanes;     /* lanes per 1-D transform (threads per transform)          */
+  int32_t radix_a;   /* the transform's split m = radix_a * radix_b: the radices */
+  int32_t radix_b;   /*   of its two register passes                             */
+  int32_t pad0;
 } fpm_tune_entry;
 
 /* Most candidates fpm_autotune times; an `entries` array this long receives them all. */

@@ -68,14 +68,16 @@ class PlanInfo(C.Structure):
 
 class TuneEntry(C.Structure):
     _fields_ = [("mode", C.c_int32), ("threads", C.c_int32), ("cluster", C.c_int32), ("branches", C.c_int32),
-                ("ms", C.c_double)]
+                ("ms", C.c_double), ("lanes", C.c_int32), ("radix_a", C.c_int32), ("radix_b", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("load_launches", C.c_int64), ("run_launches", C.c_int64), ("update_launches", C.c_int64),
                 ("updates", C.c_int64), ("update_ms", C.c_double), ("device_error", C.c_int32),
                 ("persistent_clusters", C.c_int32), ("run_threads", C.c_int32), ("online_launched", C.c_int32),
-                ("online_steps", C.c_int32), ("run_cluster", C.c_int32), ("merge_ms", C.c_double)]
+                ("online_steps", C.c_int32), ("run_cluster", C.c_int32), ("merge_ms", C.c_double),
+                ("run_lanes", C.c_int32), ("pad0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -242,8 +244,8 @@ class Plan:
         _check(_lib.fpm_autotune(self._h, int(iters), _stream(stream), ent, TUNE_MAX_ENTRIES, C.byref(n),
                                  C.byref(best)))
         names = {v: k for k, v in RUN.items()}
-        out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "branches": e.branches, "ms": e.ms}
-               for e in ent[:n.value]]
+        out = [{"mode": names[e.mode], "threads": e.threads, "cluster": e.cluster, "branches": e.branches,
+                "lanes": e.lanes, "split": (e.radix_a, e.radix_b), "ms": e.ms} for e in ent[:n.value]]
         return out, best.value
 
     def stats(self, check: bool = True) -> dict:

@@ -360,6 +360,14 @@ bool persistent_fits(int m, int rows) {
   return std::max(persistent_smem(m, rows, m), persistent_smem(m, rows, 0)) <= 232448;
 }
 int persistent_cluster_size(int) { return kPC; }
+int persistent_lanes(int m) {
+  switch (m) {
+    case 64: return P64::TPT;
+    case 128: return P128::TPT;
+    case 192: return P192::TPT;
+    default: return P256x::TPT;
+  }
+}
 
 int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, int *clusters_out) {
   if (q->n_items == 0) return FPM_OK;

@@ -42,6 +42,8 @@ int persistent_block_threads(int m);
 bool persistent_fits(int m, int rows);
 // CTAs per cluster of the persistent kernel for a queue whose jobs all have tile side m (0: mixed).
 int persistent_cluster_size(int m);
+// Lanes per 1-D transform of the persistent kernel's update for tile side m.
+int persistent_lanes(int m);
 // Reset the counters and `err` ([0] error bits, [1] abort flag) and launch the
 // persistent kernel on `st`.  stall_test > 0 makes every dependency wait look
 // at a flag nothing sets, with a 50 ms limit (exercises the timeout path).

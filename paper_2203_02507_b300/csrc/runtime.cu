@@ -62,14 +62,21 @@ using Cfg256w = UpdateCfg<256, 16, 16, 16, 2, 384, 1>;
 using Cfg256x = UpdateCfg<256, 16, 16, 16, 2, 448, 1>;
 using Cfg256q = UpdateCfg<256, 16, 16, 16, 4, 192, 2, 1, 1>;
 using Cfg256o = UpdateCfg<256, 16, 16, 16, 4, 256, 2, 1, 0, 1>;
+// eight lanes per transform (two radix units per lane and pass): the autotuner's
+// threads-per-transform choice
+using Cfg256e = UpdateCfg<256, 16, 16, 8, 4, 128, 2, 1, 0, 1>;
+using Cfg128e = UpdateCfg<128, 16, 8, 4, 2, 128, 2, 1, 0, 1>;
+using Cfg64e = UpdateCfg<64, 8, 8, 4, 1, 128, 2>;
 
 static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {
       make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg64c2>(), make_variant<Cfg64c4>(),  // 64
+      make_variant<Cfg64e>(),
       make_variant<Cfg128o>(), make_variant<Cfg128t>(), make_variant<Cfg128>(),  make_variant<Cfg128w>(),  // 128
+      make_variant<Cfg128e>(),
       make_variant<Cfg192h>(), make_variant<Cfg192o>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),  // 192
       make_variant<Cfg256o>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256w>(),
-      make_variant<Cfg256>()};                                                                          // 256
+      make_variant<Cfg256>(),  make_variant<Cfg256e>()};                                                // 256
   return v;
 }
 
@@ -80,10 +87,11 @@ static constexpr size_t kMaxSmem = 232448;   // 227 KB per CTA on sm_103a
 // thread count and cluster size ("256x4").
 static const Variant *find_variant(int m, int rows) {
   const char *env = getenv("FPM_UPDATE_THREADS");
-  int want = 0, want_c = 0;
-  if (env && sscanf(env, "%dx%d", &want, &want_c) < 1) want = 0;
+  int want = 0, want_c = 0, want_l = 0;
+  if (env && sscanf(env, "%dx%d/%d", &want, &want_c, &want_l) < 1) want = 0;
   for (const auto &v : variants())
-    if (v.m == m && v.smem(rows) <= kMaxSmem && (want == 0 || v.t == want) && (want_c == 0 || v.c == want_c))
+    if (v.m == m && v.smem(rows) <= kMaxSmem && (want == 0 || v.t == want) && (want_c == 0 || v.c == want_c) &&
+        (want_l == 0 || v.tpt == want_l))
       return &v;
   for (const auto &v : variants())
     if (v.m == m && v.smem(rows) <= kMaxSmem) return &v;
@@ -200,7 +208,9 @@ struct DeviceState {
   std::map<GraphKey, int32_t> graph_threads;      // update-kernel threads captured in each graph
   int32_t run_threads = 0;                        // of the last fpm_reconstruct (fpm_get_stats)
   int32_t run_cluster = 0;
+  int32_t run_lanes = 0;
   std::map<GraphKey, int32_t> graph_cluster;      // its CTAs per cluster
+  std::map<GraphKey, int32_t> graph_lanes;        // its lanes per transform
   // counters (fpm_get_stats)
   int64_t load_launches = 0, run_launches = 0;
   std::vector<cudaEvent_t> events;            // 2 per wave step of a timed run
@@ -1006,6 +1016,8 @@ int get_stats(fpm_plan *p, fpm_stats *out) {
   out->persistent_clusters = d->persistent_clusters;
   out->run_threads = d->run_threads;
   out->run_cluster = d->run_cluster;
+  out->run_lanes = d->run_lanes;
+  out->pad0 = 0;
   online_progress(p, &out->online_launched, &out->online_steps);
   const int derr = device_error(p);
   out->device_error = derr == FPM_ETIMEOUT ? FPM_ETIMEOUT : 0;
@@ -1191,6 +1203,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   if (base == FPM_RUN_PERSISTENT) {
     d->run_threads = fpm::persistent_block_threads(p->m);
     d->run_cluster = fpm::persistent_cluster_size(p->m);
+    d->run_lanes = fpm::persistent_lanes(p->m);
     return fpm::run_persistent(p, iters, st, graph, stall);
   }
   if (!graph) {
@@ -1199,6 +1212,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     d->run_launches = nl;
     d->run_threads = d->var->t;
     d->run_cluster = d->var->c;
+    d->run_lanes = d->var->tpt;
     return rc;
   }
   const int branches = (base == FPM_RUN_WAVES && !timed) ? std::min(d->branches, std::max(1, p->n_tiles)) : 1;
@@ -1222,6 +1236,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
     d->graph_launches[key] = nl;
     d->graph_threads[key] = d->var->t;
     d->graph_cluster[key] = d->var->c;
+    d->graph_lanes[key] = d->var->tpt;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (own) cudaStreamDestroy(cap);
@@ -1253,6 +1268,7 @@ int fpm_reconstruct(fpm_plan *p, int32_t iters, int32_t mode, void *stream) {
   d->run_launches = d->graph_launches[key];
   d->run_threads = d->graph_threads[key];
   d->run_cluster = d->graph_cluster[key];
+  d->run_lanes = d->graph_lanes[key];
   return FPM_OK;
 }
 
@@ -1375,6 +1391,12 @@ int fpm_autotune(fpm_plan *p, int32_t iters, void *stream, fpm_tune_entry *entri
       entries[i].cluster = c.v ? c.v->c : fpm::persistent_cluster_size(p->m);
       entries[i].branches = c.branches;
       entries[i].ms = c.ms;
+      int va = 0, vb = 0, vc = 0, vt = 0;
+      fpm::update_variant(p->m, rows, &va, &vb, &vc, &vt);          // the persistent kernel's split is the same
+      entries[i].lanes = c.v ? c.v->tpt : fpm::persistent_lanes(p->m);
+      entries[i].radix_a = c.v ? c.v->a : va;
+      entries[i].radix_b = c.v ? c.v->b : vb;
+      entries[i].pad0 = 0;
     }
   if (best) *best = bi;
   return FPM_OK;

@@ -255,6 +255,9 @@ def test_autotune_keeps_state_and_picks_a_bit_identical_path():
     entries, best = p.autotune(iters=1)
     assert len(entries) >= 3 and all(e["ms"] > 0 for e in entries) and 0 <= best < len(entries)
     assert {e["mode"] for e in entries} == {"waves", "persistent"}
+    # the threads-per-transform choice: wave variants with different lanes per transform
+    assert len({e["lanes"] for e in entries if e["mode"] == "waves"}) >= 2
+    assert all(e["split"][0] * e["split"][1] == j.w.tile for e in entries)
     for t in range(j.w.n_tiles):                        # the trials left the state as it was
         assert np.array_equal(p.spectrum(t), before[t])
     p.reconstruct(2, mode="auto", graph=True)
@@ -322,21 +325,22 @@ def test_graph_branches_over_tile_groups_are_bit_identical(monkeypatch):
             assert np.array_equal(a, c)
 
 
-# threads per CTA x CTAs per cluster of every update-kernel variant of a tile side
+# threads per CTA x CTAs per cluster / lanes per transform of every update-kernel
+# variant of a tile side
 VARIANTS = {
-    "m64_epry": ("128x1", "256x1", "128x2", "128x4"),
-    "m128_epry": ("128x1", "256x1", "256x2", "128x2"),
-    "m192_epry": ("256x1", "256x2", "192x2", "256x4"),
-    "m256_epry": ("256x4", "448x2", "384x2", "256x2", "192x4"),
+    "m64_epry": ("128x1/8", "256x1/8", "128x2/8", "128x4/8", "128x1/4"),
+    "m128_epry": ("128x1/8", "256x1/8", "256x2/8", "128x2/8", "128x2/4"),
+    "m192_epry": ("256x1/16", "256x2/16", "192x2/16", "256x4/16"),
+    "m256_epry": ("256x4/16", "448x2/16", "384x2/16", "256x2/16", "192x4/16", "128x4/8"),
 }
 
 
 @pytest.mark.parametrize("name", list(VARIANTS))
 def test_update_kernel_variants_are_bit_identical(name, monkeypatch):
     """Every update-kernel variant of a tile side (threads per CTA, CTAs per
-    cluster, CTAs per SM, twiddles in shared or global memory, row prefetch)
-    runs the same per-row and per-column arithmetic: the same state bit for bit,
-    whichever variant the autotuner picks."""
+    cluster, CTAs per SM, lanes per transform, twiddles in shared or global
+    memory, row prefetch) runs the same per-row and per-column arithmetic: the
+    same state bit for bit, whichever variant the autotuner picks."""
     j = job(name)
     outs = []
     for sel in VARIANTS[name]:
@@ -345,8 +349,10 @@ def test_update_kernel_variants_are_bit_identical(name, monkeypatch):
         p.load_tiles(j.stack, j.counts_per_unit)
         p.reconstruct(2, mode="waves", graph=True)
         st = p.stats()
-        assert (st["run_threads"], st["run_cluster"]) == tuple(int(v) for v in sel.split("x"))
-        assert p.info["cluster"] == int(sel.split("x")[1])
+        t, rest = sel.split("x")
+        c, lanes = rest.split("/")
+        assert (st["run_threads"], st["run_cluster"], st["run_lanes"]) == (int(t), int(c), int(lanes))
+        assert p.info["cluster"] == int(c)
         outs.append([p.spectrum(t_) for t_ in range(j.w.n_tiles)] + [p.pupil(t_) for t_ in range(j.w.n_tiles)])
         p.close()
     for o in outs[1:]:
