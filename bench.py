@@ -43,10 +43,10 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFL
 # as it stands; a launch scales it by the updates it processes.  Emptied
 # whenever the kernel changes until re-captured.
 TRAFFIC_PER_UPDATE = {
-    # profiles/update_kernel_m256_4cta256_ncu_full.md: 12,634,880 + 0 B for 32 updates
-    ("waves", 256, 256, 4): (12634880 + 0) / 32,
+    # profiles/update_kernel_m256_4cta256_ncu_full.md: 12,635,648 + 256 B for 32 updates
+    ("waves", 256, 256, 4): (12635648 + 256) / 32,
     # (the captures of the 448 x 2, 192 x 4 and persistent kernels in profiles/ predate the
-    # amplitude-step change, so their variants report no traffic until re-captured)
+    # amplitude-step and packed-addition changes, so their variants report no traffic until re-captured)
 }
 
 EXTRA = {
