@@ -133,8 +133,13 @@ __device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem)
 // One update; all threads of all C CTAs of the cluster call this with the same item.
 // Shared memory: [twiddles 2m (not with Cfg::TG)][normaliser partials][inter R x W][exchange scratch].
 // load_tw = false keeps the twiddles of an earlier update with the same m.
+// ordered_end = true: the closing cluster barrier also orders this update's global
+// writes before whatever the cluster does next (the persistent kernel signals
+// completion right after); false: the barrier only keeps the CTAs' shared memory
+// alive until the cluster has read it, and the kernel's end orders the writes.
 template <class Cfg, typename Img>
-__device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem, bool load_tw = true) {
+__device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem, bool load_tw = true,
+                                           bool ordered_end = true) {
   constexpr int M = Cfg::M, A = Cfg::A, B = Cfg::B, TPT = Cfg::TPT, C = Cfg::C, T = Cfg::T;
   constexpr int W = Cfg::W, G = Cfg::G, SCR = Cfg::SCR;
   const int rows = a.rows;
@@ -484,7 +489,12 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   }
   // keep this CTA's shared memory alive until the cluster is done reading it
   if constexpr (C > 1) {
-    cg::this_cluster().sync();
+    if (ordered_end) {
+      cg::this_cluster().sync();
+    } else {
+      // relaxed arrive: no wait for this thread's global stores to drain
+      asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+    }
   }
 }
 
@@ -492,7 +502,7 @@ template <class Cfg, typename Img>
 __global__ void __launch_bounds__(Cfg::T, Cfg::MINB) update_kernel(const __grid_constant__ UpdateArgs a, long long item0) {
   extern __shared__ float4 smem_raw[];
   const int4 item = a.items[item0 + blockIdx.x / Cfg::C];
-  run_update<Cfg, Img>(a, item, reinterpret_cast<float2 *>(smem_raw));
+  run_update<Cfg, Img>(a, item, reinterpret_cast<float2 *>(smem_raw), true, false);
 }
 
 }  // namespace fpm
