@@ -442,8 +442,10 @@ def stitch_timing(plan, torch, dev, stack, k, w, reps=3):
     gbs = nbytes / (ms / 1e3) / 1e9
     return {"ms": ms, "fov": [info["fov_h"], info["fov_w"]], "hr_overlap": info["hr_overlap"],
             "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_peak_gbs": peak, "frac": gbs / peak, "peak_source": src,
-            "includes": "per-tile N x N inverse FFTs (line FFT kernel), band sums, assembly; temporaries allocated "
-                        "stream-ordered"}
+            "includes": "one tile column at a time: row transforms of its spectra (with each row's band values), "
+                        "its band sums and Eq. 1 weights on the device, column transforms writing weight x object "
+                        "straight into the image; the row transforms' output waits in L2; scratch kept with the "
+                        "plan"}
 
 
 def uneven_batch(torch, dev, steps=3):

@@ -18,9 +18,15 @@ constexpr int kMaxRadices = 12;
 
 struct FftLines {
   float2 *data;                // output lines (and input, unless src is set)
-  const float2 *src;           // input lines at the same offsets, or null (in place)
+  const float2 *src;           // input lines at the same offsets within a batch, or null (in place)
   const float2 *tw;            // [len] exp(sign 2 pi i j / len)
+  // optional, lengths 256 and 1024: the same twiddles in the order the register
+  // kernel's passes read them, so that a warp's loads share cache lines:
+  // [(r - 1) 16 + k] = tw[k r len / 256] (r < 16, k < 16), then for length 1024
+  // [240 + (r - 1) 256 + j] = tw[j r] (r < 4, j < 256)
+  const float2 *tw_pass;
   long long batch_stride;      // elements between batches
+  long long src_batch_stride;  // elements between batches of src (the launcher sets batch_stride when 0)
   long long line_stride;       // elements between lines of a batch
   long long elem_stride;       // elements between samples of a line
   int lines_per_batch;
@@ -31,13 +37,104 @@ struct FftLines {
                                // together so each 32-byte sector is used whole
   float finish;                // 0, or: output (e, l) times finish * (-1)^(e + l),
                                // e the sample and l the line index within its batch
+  // Field-of-view output (strided lines only, one batch = one tile): with fov set,
+  // output sample e of line l of batch b is not stored in `data` but, where it
+  // lies in the rows and columns tile t = fov_tile0 + b keeps, multiplied by
+  // fov_weight[t] into the stitched image at (i (N - ov) + e, j (N - ov) + l),
+  // (i, j) = the tile's grid position, N = len.
+  float2 *fov;
+  const float2 *fov_weight;
+  long long fov_w;             // row length of the stitched image
+  int fov_ov, fov_tiles_y, fov_tiles_x, fov_tile0;
+  int fov_tile_step;           // tile index step from one batch to the next (the launcher sets 1 when 0)
+  // Band sums of contiguous lines (elem_stride 1): with band set, line l of the
+  // launch also writes band[3 l + 0] = sum_{e < band_ov} (-1)^e y_e,
+  // band[3 l + 1] = sum_{e >= len - band_ov} (-1)^e y_e (y the output before
+  // any finish) and band[3 l + 2] = its input sample len / 2.
+  float2 *band;
+  int band_ov;
 };
+
+// Rows [r0, r1) that tile row i (of k_tiles, N = n, shared band ov) keeps in the
+// stitched image (Eq. 1 read as: a neighbour pair's first image up to r - ov/2).
+__host__ __device__ inline void stitch_kept(int i, int k_tiles, int n, int ov, int *r0, int *r1) {
+  *r0 = i > 0 ? ov - ov / 2 : 0;
+  *r1 = i < k_tiles - 1 ? n - ov / 2 : n;
+}
+
+// Where the lines a CTA stores go: every line of a CTA lies in one batch, so
+// with a field-of-view output the tile, its grid position, the rows and the
+// columns it keeps are fixed per CTA (computed once by line_target).
+struct LineTarget {
+  float2 *dst;                 // sample e of line l0 + c lands at dst[e * es + c]
+  long long es;
+  int y0, y1, x0, x1;          // kept samples e in [y0, y1), lines l0 + c in [x0, x1)
+  int l0;
+  float2 w;                    // tile weight
+};
+__device__ __forceinline__ LineTarget line_target(const FftLines &f, float2 *base, long long line_first) {
+  LineTarget lt;
+  if (!f.fov) {
+    lt.dst = base;
+    lt.es = f.elem_stride;
+    lt.y0 = 0;
+    lt.y1 = 1 << 30;
+    lt.x0 = 0;
+    lt.x1 = 1 << 30;
+    lt.l0 = 0;
+    lt.w = make_float2(1.f, 0.f);
+    return lt;
+  }
+  const int b = (int)(line_first / f.lines_per_batch);
+  const int x = (int)(line_first - (long long)b * f.lines_per_batch);
+  const int t = f.fov_tile0 + b * f.fov_tile_step, i = t / f.fov_tiles_x, j = t - i * f.fov_tiles_x;
+  const int stride = f.len - f.fov_ov;
+  stitch_kept(i, f.fov_tiles_y, f.len, f.fov_ov, &lt.y0, &lt.y1);
+  stitch_kept(j, f.fov_tiles_x, f.len, f.fov_ov, &lt.x0, &lt.x1);
+  lt.l0 = x;
+  lt.dst = f.fov + (long long)i * stride * f.fov_w + (long long)j * stride + x;
+  lt.es = f.fov_w;
+  lt.w = f.fov_weight[t];
+  return lt;
+}
+// Store of finished output sample e of the CTA's line c.
+__device__ __forceinline__ void line_store(const FftLines &f, const LineTarget &lt, int e, int c, float2 v) {
+  if (!f.fov) {
+    lt.dst[(long long)e * lt.es + c] = v;
+    return;
+  }
+  if (e < lt.y0 || e >= lt.y1 || lt.l0 + c < lt.x0 || lt.l0 + c >= lt.x1) return;
+  __stcs(lt.dst + (long long)e * lt.es + c, cmul(lt.w, v));   // written once: evict first
+}
+
+// Band sums of one line from its outputs: (-1)^e y_e over e < ov and over
+// e >= len - ov, accumulated into *lo / *hi.
+__device__ __forceinline__ void band_add(float2 y, int e, int len, int ov, float2 *lo, float2 *hi) {
+  if (e >= ov && e < len - ov) return;
+  const float2 v = (e & 1) ? make_float2(-y.x, -y.y) : y;
+  if (e < ov) *lo = make_float2(__fadd_rn(lo->x, v.x), __fadd_rn(lo->y, v.y));
+  else *hi = make_float2(__fadd_rn(hi->x, v.x), __fadd_rn(hi->y, v.y));
+}
+// Sum over the `width` consecutive lanes of a warp (width a power of 2 <= 32), fixed order.
+template <int W>
+__device__ __forceinline__ float2 lanes_sum(float2 a) {
+#pragma unroll
+  for (int s = W / 2; s > 0; s >>= 1) {
+    a.x = __fadd_rn(a.x, __shfl_xor_sync(0xffffffffu, a.x, s));
+    a.y = __fadd_rn(a.y, __shfl_xor_sync(0xffffffffu, a.y, s));
+  }
+  return a;
+}
 
 // Shared-memory position of line sample i: one pad slot per 16 samples, so a
 // butterfly's R outputs written with unit stride by consecutive threads (the
 // first Stockham pass) fall in different banks.
 __device__ __forceinline__ int line_pad(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int line_padded_len(int len) { return len + len / 16 + 1; }
+// Spacing of lines in shared memory: a half-warp moving a strided tile touches
+// g adjacent lines at 16 / g samples each, which fall in distinct bank pairs when
+// the spacing is odd for g = 16 and 2 mod 16 for g = 8 (and for 4 lines at twice
+// the spacing).
+__host__ __device__ constexpr int line_padded_len(int len, int g = 8) { return len + len / 16 + (g == 16 ? 1 : 2); }
 
 // Stockham pass: R-point butterflies on strided inputs, autosorted outputs,
 // butterflies j = t, t + nt, ... done by threads t of a group of nt.
@@ -69,11 +166,12 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
   constexpr int lpc = LPC;
   const int len = f.len;
   const long long line0 = (long long)blockIdx.x * lpc;
-  const long long off = (line0 / f.lines_per_batch) * f.batch_stride + (line0 % f.lines_per_batch) * f.line_stride;
+  const long long b0i = line0 / f.lines_per_batch, loff = (line0 % f.lines_per_batch) * f.line_stride;
+  const long long off = b0i * f.batch_stride + loff;
   const int l0 = (int)(line0 % f.lines_per_batch);
   const int plen = line_padded_len(len);
   float2 *base = f.data + off;
-  const float2 *in = (f.src ? f.src : f.data) + off;
+  const float2 *in = f.src ? f.src + b0i * f.src_batch_stride + loff : f.data + off;
   // sample e of line c at e * elem_stride + c (adjacent lines: line_stride 1)
   for (int i = threadIdx.x; i < len * lpc; i += blockDim.x) {
     const int e = i / lpc, c = i - e * lpc;
@@ -83,6 +181,7 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
   // the CTA's threads form lpc groups, one per line; passes run in lockstep
   const int nt = blockDim.x / lpc, grp = threadIdx.x / nt, t = threadIdx.x - grp * nt;
   float2 *b0 = line_buf + (size_t)grp * 2 * plen;
+  const float2 mid = b0[line_pad(len / 2)];           // the input sample len / 2 (band sums)
   int cur = 0, ns = 1;
   for (int p = 0; p < f.nrad; ++p) {
     const int r = f.radix[p];
@@ -96,6 +195,23 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
     cur ^= 1;
     __syncthreads();
   }
+  if (f.band && t < 32) {
+    // the first warp of each line's group: band sums in a fixed order
+    float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+    const float2 *yl = b0 + cur * plen;
+    for (int e = t; e < f.band_ov; e += 32) band_add(yl[line_pad(e)], e, len, f.band_ov, &lo, &hi);
+    for (int e = len - f.band_ov + t; e < len; e += 32)
+      if (e >= f.band_ov) band_add(yl[line_pad(e)], e, len, f.band_ov, &lo, &hi);
+    lo = lanes_sum<32>(lo);
+    hi = lanes_sum<32>(hi);
+    if (t == 0) {
+      float2 *bo = f.band + 3 * (line0 + grp);
+      bo[0] = lo;
+      bo[1] = hi;
+      bo[2] = mid;
+    }
+  }
+  const LineTarget lt = line_target(f, base, line0);
   for (int i = threadIdx.x; i < len * lpc; i += blockDim.x) {
     const int e = i / lpc, c = i - e * lpc;
     float2 v = line_buf[(size_t)c * 2 * plen + cur * plen + line_pad(e)];
@@ -103,7 +219,7 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
       const float sc = ((e + l0 + c) & 1) ? -f.finish : f.finish;
       v = make_float2(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc));
     }
-    base[(long long)e * f.elem_stride + c] = v;
+    line_store(f, lt, e, c, v);
   }
 }
 
@@ -114,37 +230,67 @@ __global__ void fft_lines_kernel(const __grid_constant__ FftLines f) {
 // stored straight to it where the lines are contiguous (elem_stride 1).  Lines
 // whose samples are strided (line_stride 1, elem_stride > 1) are staged through
 // shared memory G adjacent lines at a time, so every 32-byte sector is used
-// whole.  G lines per CTA, LEN / 16 threads per line; shared memory G *
-// line_padded_len(LEN) float2 (one buffer, a barrier between the reads and the
+// whole.  G lines per CTA, LEN / 16 threads per line; TP: twiddles from
+// f.tw_pass; shared memory G * line_padded_len(LEN, G) float2 (one buffer, a barrier between the reads and the
 // writes of each pass).
-template <int S, int LEN, int G>
-__global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
+template <int S, int LEN, int G, bool TP>
+__global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 4)
     fft_lines_reg_kernel(const __grid_constant__ FftLines f) {
   static_assert(LEN == 256 || LEN == 1024, "lengths 16 x 16 and 16 x 16 x 4");
   constexpr int NT = LEN / 16;                 // threads per line
-  constexpr int PL = line_padded_len(LEN);
+  constexpr int PL = line_padded_len(LEN, G);
   extern __shared__ float2 line_buf[];
   const int g = threadIdx.x / NT, t = threadIdx.x - g * NT;
   const long long line0 = (long long)blockIdx.x * G;
-  const bool rows = f.elem_stride == 1;
+  // (1024-sample lines in groups of 8 are always strided: the launcher takes 4 for rows)
+  const bool rows = (LEN != 1024 || G != 8) && f.elem_stride == 1;
   // rows: each group's own line; strided: G adjacent lines of one batch
   const long long line = rows ? line0 + g : line0;
-  const long long off = (line / f.lines_per_batch) * f.batch_stride + (line % f.lines_per_batch) * f.line_stride;
+  const long long bi = line / f.lines_per_batch, loff = (line % f.lines_per_batch) * f.line_stride;
+  const long long off = bi * f.batch_stride + loff;
   const int lb = (int)(line % f.lines_per_batch);     // index of the (first) line within its batch
-  const float2 *in = (f.src ? f.src : f.data) + off;
+  const float2 *in = f.src ? f.src + bi * f.src_batch_stride + loff : f.data + off;
   float2 *out = f.data + off;
   float2 *xs = line_buf + (size_t)g * PL;
+  __shared__ float2 band_red[G][(NT + 31) / 32][2];
+  // band sums of contiguous lines: partial sums of each thread, then of the line
+  auto band_out = [&](float2 lo, float2 hi, float2 mid) {
+    constexpr int W = NT < 32 ? NT : 32;
+    lo = lanes_sum<W>(lo);
+    hi = lanes_sum<W>(hi);
+    if constexpr (NT > 32) {
+      if ((t & 31) == 0) {
+        band_red[g][t >> 5][0] = lo;
+        band_red[g][t >> 5][1] = hi;
+      }
+      __syncthreads();
+      if (t == 0)
+        for (int w = 1; w < NT / 32; ++w) {
+          lo = cadd(lo, band_red[g][w][0]);
+          hi = cadd(hi, band_red[g][w][1]);
+        }
+    }
+    if (t == 0) {
+      float2 *bo = f.band + 3 * line;
+      bo[0] = lo;
+      bo[1] = hi;
+      bo[2] = mid;
+    }
+  };
   float2 v[16];
+  float2 mid = make_float2(0.f, 0.f);
   if (rows) {
+    // spectra are read once: evict first
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = in[t + r * NT];
+    for (int r = 0; r < 16; ++r) v[r] = __ldcs(in + t + r * NT);
+    mid = v[8];                                   // sample LEN / 2 = 8 NT (thread 0)
   } else {
     // 16 loads a thread, all in flight before their shared-memory stores
     float2 u[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int i = threadIdx.x + q * G * NT, e = i / G, c = i - e * G;
-      u[q] = in[(long long)e * f.elem_stride + c];
+      u[q] = __ldcs(in + (long long)e * f.elem_stride + c);
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -167,7 +313,7 @@ __global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     v[r] = xs[line_pad(t + r * NT)];
-    if (r > 0 && k2 > 0) v[r] = cmul(v[r], f.tw[k2 * r * step2]);
+    if (r > 0 && k2 > 0) v[r] = cmul(v[r], TP ? f.tw_pass[(r - 1) * 16 + k2] : f.tw[k2 * r * step2]);
   }
   Dft<16, S>::run(v);
   const int base2 = (t / 16) * 256 + k2;
@@ -179,6 +325,12 @@ __global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
   };
   if constexpr (LEN == 256) {
     if (rows) {
+      if (f.band) {
+        float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) band_add(v[r], base2 + 16 * r, LEN, f.band_ov, &lo, &hi);
+        band_out(lo, hi, mid);
+      }
 #pragma unroll
       for (int r = 0; r < 16; ++r) out[base2 + 16 * r] = finish(v[r], base2 + 16 * r, 0);
       return;
@@ -199,11 +351,19 @@ __global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         w[q][r] = xs[line_pad(j + 256 * r)];
-        if (r > 0 && j > 0) w[q][r] = cmul(w[q][r], f.tw[j * r]);
+        if (r > 0 && j > 0) w[q][r] = cmul(w[q][r], TP ? f.tw_pass[240 + (r - 1) * 256 + j] : f.tw[j * r]);
       }
       Dft<4, S>::run(w[q]);
     }
     if (rows) {
+      if (f.band) {
+        float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) band_add(w[q][r], t + NT * q + 256 * r, LEN, f.band_ov, &lo, &hi);
+        band_out(lo, hi, mid);
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -221,10 +381,28 @@ __global__ void __launch_bounds__(G *(LEN / 16), G *(LEN / 16) >= 512 ? 2 : 3)
   }
   // strided lines: the G lines leave through shared memory, adjacent lines together
   __syncthreads();
+  const LineTarget lt = line_target(f, out, line);
+  if (f.fov) {
+    // a thread stores samples e0 + q NT of line c: one column, one sign parity
+    // (NT is even), so the kept-column test and weight x finish x sign are per thread
+    const int c = threadIdx.x % G, e0 = threadIdx.x / G;
+    if (lt.l0 + c < lt.x0 || lt.l0 + c >= lt.x1) return;
+    float2 wt = lt.w;
+    if (f.finish != 0.f) {
+      const float sc = ((e0 + lb + c) & 1) ? -f.finish : f.finish;
+      wt = make_float2(__fmul_rn(wt.x, sc), __fmul_rn(wt.y, sc));
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = e0 + q * NT;
+      if (e >= lt.y0 && e < lt.y1) __stcs(lt.dst + (long long)e * lt.es + c, cmul(wt, line_buf[(size_t)c * PL + line_pad(e)]));
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int i = threadIdx.x + q * G * NT, e = i / G, c = i - e * G;
-    out[(long long)e * f.elem_stride + c] = finish(line_buf[(size_t)c * PL + line_pad(e)], e, c);
+    line_store(f, lt, e, c, finish(line_buf[(size_t)c * PL + line_pad(e)], e, c));
   }
 }
 

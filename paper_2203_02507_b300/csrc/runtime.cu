@@ -192,6 +192,7 @@ struct DeviceState {
   int2 *shifts = nullptr, *origins = nullptr, *chords = nullptr;
   float2 *tw_inv = nullptr, *tw_fwd = nullptr;      // update kernel split
   float2 *twl_fwd_m = nullptr;                      // line FFT tables
+  float2 *stitch_tab = nullptr;                     // tables of the stitch (built on its first call)
 
   unsigned *err = nullptr;
   void *images = nullptr;                          // [T][L][m][m] column layout (tile_image_offset)
@@ -260,7 +261,7 @@ void destroy_device_state(fpm_plan *p) {
     dfree(s.merges);
   }
   for (void *q : {(void *)d->spec, (void *)d->pup, (void *)d->pup0, (void *)d->dpup, (void *)d->shifts, (void *)d->origins,
-                  (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->err,
+                  (void *)d->chords, (void *)d->tw_inv, (void *)d->tw_fwd, (void *)d->twl_fwd_m, (void *)d->stitch_tab, (void *)d->err,
                   d->images, d->scratch})
     dfree(q);
   if (cur >= 0) cudaSetDevice(cur);
@@ -331,41 +332,50 @@ int ensure_device_state(fpm_plan *p) {
 }
 
 // Batched 1-D FFTs over lines of a device array.
-int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int len, int sign, long long n_lines,
-                        int lines_per_batch, long long batch_stride, long long line_stride, long long elem_stride,
-                        float finish, cudaStream_t st) {
-  FftLines f{};
-  f.data = data;
-  f.src = src;
-  f.tw = tw;
-  f.len = len;
-  f.batch_stride = batch_stride;
-  f.line_stride = line_stride;
-  f.elem_stride = elem_stride;
-  f.lines_per_batch = lines_per_batch;
-  f.finish = finish;
+// Launch the line transforms described by f (data, src, tw, len, strides, lines
+// per batch, finish and the optional field-of-view output already set).
+static int launch_lines(FftLines f, int sign, long long n_lines, cudaStream_t st) {
+  const int len = f.len;
+  if (f.src_batch_stride == 0) f.src_batch_stride = f.batch_stride;
+  if (f.fov_tile_step == 0) f.fov_tile_step = 1;
+  const long long lines_per_batch = f.lines_per_batch, batch_stride = f.batch_stride;
+  const long long src_batch_stride = f.src_batch_stride;
+  float2 *const data = f.data;
+  const float2 *const src = f.src;
+  float2 *const band = f.band;
+  const int tile0 = f.fov_tile0;
   if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
+  if (band && f.elem_stride != 1) return fail(FPM_EINVAL, "internal: band sums need contiguous lines");
   // lengths 256 and 1024: butterflies in registers, G lines per CTA (rows: any lines;
   // strided samples: G adjacent lines of one batch)
   if (len == 256 || len == 1024) {
-    const bool rows = elem_stride == 1;
+    const bool rows = f.elem_stride == 1;
     // strided 1024-sample lines: 8 adjacent ones per CTA, 64-byte row segments
     const int G = len == 256 ? 16 : rows ? 4 : 8;
-    const bool cols = line_stride == 1 && lines_per_batch % G == 0;
-    if ((rows || cols) && n_lines % G == 0) {
+    const bool cols = f.line_stride == 1 && lines_per_batch % G == 0;
+    if ((rows || cols) && n_lines % G == 0 && !(rows && f.fov)) {
       void (*kern)(FftLines);
-      if (len == 256) kern = sign > 0 ? &fft_lines_reg_kernel<1, 256, 16> : &fft_lines_reg_kernel<-1, 256, 16>;
-      else if (rows) kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4> : &fft_lines_reg_kernel<-1, 1024, 4>;
-      else kern = sign > 0 ? &fft_lines_reg_kernel<1, 1024, 8> : &fft_lines_reg_kernel<-1, 1024, 8>;
-      const size_t smem = (size_t)G * line_padded_len(len) * sizeof(float2);
+      const bool tp = f.tw_pass != nullptr;
+      if (len == 256)
+        kern = tp ? (sign > 0 ? &fft_lines_reg_kernel<1, 256, 16, true> : &fft_lines_reg_kernel<-1, 256, 16, true>)
+                  : (sign > 0 ? &fft_lines_reg_kernel<1, 256, 16, false> : &fft_lines_reg_kernel<-1, 256, 16, false>);
+      else if (rows)
+        kern = tp ? (sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4, true> : &fft_lines_reg_kernel<-1, 1024, 4, true>)
+                  : (sign > 0 ? &fft_lines_reg_kernel<1, 1024, 4, false> : &fft_lines_reg_kernel<-1, 1024, 4, false>);
+      else
+        kern = tp ? (sign > 0 ? &fft_lines_reg_kernel<1, 1024, 8, true> : &fft_lines_reg_kernel<-1, 1024, 8, true>)
+                  : (sign > 0 ? &fft_lines_reg_kernel<1, 1024, 8, false> : &fft_lines_reg_kernel<-1, 1024, 8, false>);
+      const size_t smem = (size_t)G * line_padded_len(len, G) * sizeof(float2);
       FPM_CK(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       const long long max_chunk = (1LL << 30) / lines_per_batch * lines_per_batch;   // whole batches per launch
       for (long long done = 0; done < n_lines;) {
         const long long chunk = std::min<long long>(n_lines - done, max_chunk);
         FftLines g = f;
-        const long long boff = (done / lines_per_batch) * batch_stride;
-        g.data = data + boff;
-        g.src = src ? src + boff : nullptr;
+        const long long bdone = done / lines_per_batch;
+        g.data = data + bdone * batch_stride;
+        g.src = src ? src + bdone * src_batch_stride : nullptr;
+        g.band = band ? band + 3 * done : nullptr;
+        g.fov_tile0 = tile0 + (int)bdone * f.fov_tile_step;
         kern<<<(unsigned)(chunk / G), G * (len / 16), smem, st>>>(g);
         done += chunk;
       }
@@ -373,9 +383,10 @@ int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int l
       return FPM_OK;
     }
   }
+  if (f.fov && f.elem_stride == 1) return fail(FPM_EINVAL, "internal: field-of-view output needs strided lines");
   // strided lines (columns): four adjacent ones per CTA, so loads and stores use whole sectors
-  f.lines_per_cta = (line_stride == 1 && elem_stride > 1 && lines_per_batch % 4 == 0 && n_lines % 4 == 0) ? 4 : 1;
-  if (!radices_for(len, f)) return fail(FPM_EINVAL, "FFT length %d not supported", len);
+  f.lines_per_cta =
+      (f.line_stride == 1 && f.elem_stride > 1 && lines_per_batch % 4 == 0 && n_lines % 4 == 0) ? 4 : 1;
   // one group of threads per line, a thread per radix-16 butterfly (whole warps)
   const int group = std::min(256, std::max(32, (len / 16 + 31) / 32 * 32));
   const int threads = group * f.lines_per_cta;
@@ -391,15 +402,76 @@ int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int l
     // offset the bases so that line indices restart at a batch boundary
     const long long first = done;
     if (first % lines_per_batch != 0) return fail(FPM_EINVAL, "internal: FFT chunk not batch aligned");
-    const long long off = (first / lines_per_batch) * batch_stride;
-    g.data = data + off;
-    g.src = src ? src + off : nullptr;
+    const long long bdone = first / lines_per_batch;
+    g.data = data + bdone * batch_stride;
+    g.src = src ? src + bdone * src_batch_stride : nullptr;
+    g.band = band ? band + 3 * first : nullptr;
+    g.fov_tile0 = tile0 + (int)bdone * f.fov_tile_step;
     const unsigned ctas = (unsigned)(chunk / f.lines_per_cta);
     kern<<<ctas, threads, smem, st>>>(g);
     done += chunk;
   }
   FPM_CK(cudaGetLastError());
   return FPM_OK;
+}
+
+int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int len, int sign, long long n_lines,
+                        int lines_per_batch, long long batch_stride, long long line_stride, long long elem_stride,
+                        float finish, cudaStream_t st) {
+  FftLines f{};
+  f.data = data;
+  f.src = src;
+  f.tw = tw;
+  f.len = len;
+  f.batch_stride = batch_stride;
+  f.line_stride = line_stride;
+  f.elem_stride = elem_stride;
+  f.lines_per_batch = lines_per_batch;
+  f.finish = finish;
+  return launch_lines(f, sign, n_lines, st);
+}
+
+int launch_fft_rows_banded(float2 *data, const float2 *src, const float2 *tw, const float2 *tw_pass, int n, int sign,
+                           int tiles, long long src_tile_stride, float2 *band, int ov, cudaStream_t st) {
+  FftLines f{};
+  f.data = data;
+  f.src = src;
+  f.tw = tw;
+  f.tw_pass = tw_pass;
+  f.len = n;
+  f.batch_stride = (long long)n * n;
+  f.src_batch_stride = src_tile_stride;
+  f.line_stride = n;
+  f.elem_stride = 1;
+  f.lines_per_batch = n;
+  f.band = band;
+  f.band_ov = ov;
+  return launch_lines(f, sign, (long long)tiles * n, st);
+}
+
+int launch_fft_columns_to_fov(const float2 *data, const float2 *tw, const float2 *tw_pass, int n, int sign, int tiles,
+                              float finish, float2 *fov, const float2 *weight, long long fov_w, int ov, int tiles_y,
+                              int tiles_x, int tile0, int tile_step, cudaStream_t st) {
+  FftLines f{};
+  f.data = const_cast<float2 *>(data);      // read only: the output goes to fov
+  f.src = nullptr;
+  f.tw = tw;
+  f.tw_pass = tw_pass;
+  f.len = n;
+  f.batch_stride = (long long)n * n;
+  f.line_stride = 1;
+  f.elem_stride = n;
+  f.lines_per_batch = n;
+  f.finish = finish;
+  f.fov = fov;
+  f.fov_weight = weight;
+  f.fov_w = fov_w;
+  f.fov_ov = ov;
+  f.fov_tiles_y = tiles_y;
+  f.fov_tiles_x = tiles_x;
+  f.fov_tile0 = tile0;
+  f.fov_tile_step = tile_step;
+  return launch_lines(f, sign, (long long)tiles * n, st);
 }
 
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
@@ -543,6 +615,7 @@ int plan_image_dtype(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p-
 unsigned *plan_error_word(fpm_plan *p) { return p->dev ? p->dev->err : nullptr; }
 
 const float2 *plan_spectra(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->spec : nullptr; }
+float2 **plan_stitch_tables(fpm_plan *p) { return p->dev ? &p->dev->stitch_tab : nullptr; }
 
 int plan_scratch(fpm_plan *p, size_t bytes, void **out) {
   DeviceState *d = p->dev;

@@ -16,6 +16,20 @@ std::vector<float2> twiddles_line(int len, int sign);
 int launch_fft_lines_ex(float2 *data, const float2 *src, const float2 *tw, int len, int sign, long long n_lines,
                         int lines_per_batch, long long batch_stride, long long line_stride, long long elem_stride,
                         float finish, cudaStream_t st);
+// Row transforms of `tiles` N x N tiles (N = n; tw_pass: the twiddles in pass
+// order, FftLines::tw_pass, or null) from src (tiles src_tile_stride
+// elements apart) into data (packed, N^2 apart), every row also writing its band
+// sums to band[3 l ..]: sum_{x < ov} (-1)^x y_x, sum_{x >= N - ov} (-1)^x y_x and
+// its input sample N / 2 (l = tile b's row k at b N + k).
+int launch_fft_rows_banded(float2 *data, const float2 *src, const float2 *tw, const float2 *tw_pass, int n, int sign,
+                           int tiles, long long src_tile_stride, float2 *band, int ov, cudaStream_t st);
+// Column transforms of `tiles` packed N x N tiles (N = n) whose outputs go
+// straight into the stitched image: sample (y, x) of packed tile b, which is
+// tile t = tile0 + b tile_step of the grid, times finish (-1)^(x+y) and
+// weight[t], where the tile keeps row y and column x.
+int launch_fft_columns_to_fov(const float2 *data, const float2 *tw, const float2 *tw_pass, int n, int sign, int tiles,
+                              float finish, float2 *fov, const float2 *weight, long long fov_w, int ov, int tiles_y,
+                              int tiles_x, int tile0, int tile_step, cudaStream_t st);
 int launch_fft_lines(float2 *data, const float2 *tw, int len, int sign, long long n_lines, int lines_per_batch,
                      long long batch_stride, long long line_stride, long long elem_stride, cudaStream_t st);
 struct QueueJob;
@@ -76,6 +90,9 @@ int plan_image_dtype(const fpm_plan *p);
 unsigned *plan_error_word(fpm_plan *p);
 // The plan's spectra [T][N][N] (centred complex64) once loaded, else null.
 const float2 *plan_spectra(const fpm_plan *p);
+// Slot of the plan's stitch tables (device memory freed with the plan; null
+// until the first stitch builds them), or null without device state.
+float2 **plan_stitch_tables(fpm_plan *p);
 // A device scratch buffer of at least `bytes`, kept with the plan (grown on
 // demand, freed with the plan); its contents do not survive the next call.
 int plan_scratch(fpm_plan *p, size_t bytes, void **out);

@@ -18,17 +18,30 @@
 // with T/B the sums of a tile over its first/last ov rows, and SL/SR the sums of
 // a column image over its first/last ov columns, SL(j) = sum_i c(i,j) L(i,j),
 // L(i,j) the sum of tile (i,j) over its first ov columns and the rows it keeps
-// in its column image (likewise R over the last ov columns).  The band sums are
-// reduced on the device in a fixed order (FP64 across threads), the weights
-// chained on the host in FP64, and one pass writes every output pixel as
-// weight x object.  A zero denominator (or ov = 0: no shared band) gives
-// weight 1, as in Eq. 1's reading for a dark band.
+// in its column image (likewise R over the last ov columns).  A zero
+// denominator (or ov = 0: no shared band) gives weight 1, as in Eq. 1's reading
+// for a dark band.
+//
+// The band sums need no object: the sum of o over rows Y and columns X is
+//   (1/N^2) sum_ky g_Y(ky) sum_kx O[ky][kx] h_X(kx),  g_Y(k) = sum_{y in Y} e^{2 pi i (k - N/2) y / N}
+// (likewise h_X), where the inner sum is sum_{x in X} (-1)^x R[ky][x], R the
+// natural-order inverse row transform of O, and for X = all columns it is
+// N O[ky][N/2].  So the row transforms of a tile give its band values per row
+// as they store, and the sums over ky with the closed-form g take a few
+// thousand terms per tile.  Weight c(i,j) needs only tiles above (i,j) and d(j)
+// only columns up to j, so the tiles go one tile column at a time: row
+// transforms into a buffer the size of one tile column (kept in L2: the spectra
+// are read and the image written with evict-first hints), the column's weights
+// on the device, then the column transforms write weight x object straight into
+// the stitched image, only where the tile keeps the pixel.  Every spectrum is
+// read once and every image pixel written once; no host round trip.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <complex>
 #include <vector>
 
+#include "aux_kernels.cuh"
 #include "internal.h"
 #include "runtime.h"
 
@@ -40,83 +53,151 @@ namespace fpm {
     if (e_ != cudaSuccess) return fail(FPM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-// Row range [r0, r1) that tile row i keeps in its column image of K tiles.
-__host__ __device__ inline void kept_rows(int i, int k_tiles, int n, int ov, int *r0, int *r1) {
-  *r0 = i > 0 ? ov - ov / 2 : 0;
-  *r1 = i < k_tiles - 1 ? n - ov / 2 : n;
+// Complex FP32 division by the textbook formula (|b|^2 > 0 checked by the caller).
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  const float r = __frcp_rn(__fadd_rn(__fmul_rn(b.x, b.x), __fmul_rn(b.y, b.y)));
+  return make_float2(__fmul_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), r),
+                     __fmul_rn(__fsub_rn(__fmul_rn(a.y, b.x), __fmul_rn(a.x, b.y)), r));
+}
+__device__ __forceinline__ bool cnonzero(float2 a) { return a.x != 0.f || a.y != 0.f; }
+
+// Host tables of a stitch (built once per plan, FP64 rounded to FP32), laid out
+//   [0, n)                 tw[j] = e^{+2 pi i j / n}, the inverse line FFT's twiddles
+//   [n, n + 1008)          the same twiddles in pass order (FftLines::tw_pass; n = 256, 1024)
+//   [n + 1008, 7 n + 1008) g[6][n]: g over the first ov rows, the last ov rows and
+//                          the rows kept by the four kept-row classes (class bit 0:
+//                          not the first tile row, bit 1: not the last)
+constexpr int kPassTab = 240 + 3 * 256;
+static std::vector<float2> stitch_tables(int n, int ov) {
+  using cd = std::complex<double>;
+  std::vector<float2> tab((size_t)7 * n + kPassTab, make_float2(0.f, 0.f));
+  const std::vector<float2> tw = twiddles_line(n, +1);
+  std::copy(tw.begin(), tw.end(), tab.begin());
+  if (n == 256 || n == 1024) {
+    float2 *pt = tab.data() + n;
+    for (int r = 1; r < 16; ++r)
+      for (int k = 0; k < 16; ++k) pt[(r - 1) * 16 + k] = tw[(size_t)k * r * (n / 256)];
+    if (n == 1024)
+      for (int r = 1; r < 4; ++r)
+        for (int j = 0; j < 256; ++j) pt[240 + (r - 1) * 256 + j] = tw[(size_t)j * r];
+  }
+  // e^{2 pi i j / n} and 1 - e^{2 pi i j / n} (= 2 sin^2(th/2) - i sin th), j reduced exactly
+  auto unit = [&](long long j) {
+    const long long r = ((j % n) + n) % n;
+    const double th = 2.0 * M_PI * (double)r / n;
+    return cd(std::cos(th), std::sin(th));
+  };
+  auto one_minus = [&](long long j) {
+    const long long r = ((j % n) + n) % n;
+    const double th = 2.0 * M_PI * (double)r / n, sh = std::sin(0.5 * th);
+    return cd(2.0 * sh * sh, -std::sin(th));
+  };
+  // sum_{y0 <= y < y1} e^{2 pi i f y / n}, f = k - n/2: a geometric series
+  auto series = [&](int k, int y0, int y1) {
+    const long long f = k - n / 2, len = y1 - y0;
+    cd v(0.0, 0.0);
+    if (len > 0) v = (f % n == 0) ? cd((double)len, 0.0) : unit(f * y0) * one_minus(f * len) / one_minus(f);
+    return make_float2((float)v.real(), (float)v.imag());
+  };
+  float2 *g = tab.data() + n + kPassTab;
+  for (int k = 0; k < n; ++k) {
+    g[k] = series(k, 0, ov);
+    g[(size_t)n + k] = series(k, n - ov, n);
+    for (int cls = 0; cls < 4; ++cls) {
+      const int y0 = (cls & 1) ? ov - ov / 2 : 0, y1 = (cls & 2) ? n - ov / 2 : n;
+      g[(size_t)(2 + cls) * n + k] = series(k, y0, y1);
+    }
+  }
+  return tab;
 }
 
-// Band sums of every tile in a fixed order: grid (tiles, 4, kBandChunks),
-// band 0 = first ov rows, 1 = last ov rows, 2 = first ov columns over the kept
-// rows, 3 = last ov columns over the kept rows; chunk z sums the z-th of
-// kBandChunks consecutive parts of the band.
-// out[(t * 4 + band) * kBandChunks + z] = (re, im); the host adds the chunks in order.
-constexpr int kBandThreads = 256, kBandChunks = 16;
-static __global__ void __launch_bounds__(kBandThreads) band_sums_kernel(const float2 *obj, int n, int ov,
-                                                                        int tiles_y, int tiles_x, double2 *out) {
-  __shared__ double sre[kBandThreads], sim[kBandThreads];
-  const int t = blockIdx.x, band = blockIdx.y, z = blockIdx.z;
-  const int i = t / tiles_x;
-  int y0 = 0, y1 = n, x0 = 0, x1 = n;
-  if (band == 0) y1 = ov;
-  if (band == 1) y0 = n - ov;
-  if (band >= 2) {
-    kept_rows(i, tiles_y, n, ov, &y0, &y1);
-    if (band == 2) x1 = ov;
-    else x0 = n - ov;
+// Band sums and weights of tile column j (grid ty CTAs, kWeightThreads each;
+// dynamic shared memory 5 ty float2 for the chain).  CTA i forms the four band
+// sums of tile t = i tx + j from its rows' band values (band[3 (i N + ky) ..] =
+// r_L(ky), r_R(ky), O[ky][N/2], written by the row transforms):
+//   sums[4t + 0] = (1/N)   sum_ky O[ky][N/2] g_top(ky)     (first ov rows)
+//   sums[4t + 1] = (1/N)   sum_ky O[ky][N/2] g_bot(ky)     (last ov rows)
+//   sums[4t + 2] = (1/N^2) sum_ky r_L(ky) g_kept(ky)       (first ov columns, kept rows)
+//   sums[4t + 3] = (1/N^2) sum_ky r_R(ky) g_kept(ky)       (last ov columns, kept rows)
+// each thread's terms in order, then a fixed shuffle tree.  The last CTA to
+// finish chains the weights on its first warp: the ratios B(r-1) / T(r) in
+// parallel, the running product c in row order, the products c L and c R in
+// parallel summed by a fixed tree, and d(j) from d(j-1) and SR(j-1) kept in
+// colst from the previous column.  All in FP32: the sums carry FP32 rounding
+// (about 1e-6 relative) already, and the few chained products and quotients
+// add well below that.
+constexpr int kWeightThreads = 512;
+static __global__ void __launch_bounds__(kWeightThreads)
+    stitch_weights_kernel(const float2 *band, const float2 *g, int n, int ty, int tx, int j, float2 *sums,
+                          float2 *colst, unsigned *counter, float2 *w) {
+  extern __shared__ float2 chain_sm[];              // the column's sums, then its c values
+  __shared__ float2 part[kWeightThreads / 32][4];
+  __shared__ bool last;
+  const int i = blockIdx.x, t = i * tx + j;
+  const int cls = (i > 0 ? 1 : 0) | (i < ty - 1 ? 2 : 0);
+  const float2 *g_top = g, *g_bot = g + n, *g_kept = g + (size_t)(2 + cls) * n;
+  float2 acc[4];
+  for (int b = 0; b < 4; ++b) acc[b] = make_float2(0.f, 0.f);
+  for (int ky = threadIdx.x; ky < n; ky += kWeightThreads) {
+    const float2 *bv = band + 3 * ((size_t)i * n + ky);
+    const float2 rl = bv[0], rr = bv[1], mid = bv[2];
+    acc[0] = cadd(acc[0], cmul(mid, g_top[ky]));
+    acc[1] = cadd(acc[1], cmul(mid, g_bot[ky]));
+    acc[2] = cadd(acc[2], cmul(rl, g_kept[ky]));
+    acc[3] = cadd(acc[3], cmul(rr, g_kept[ky]));
   }
-  // chunk z: rows [y0 + z rows / kBandChunks, ...) of the band, columns [x0, x1)
-  const int rows = y1 - y0;
-  const int ya = y0 + rows * z / kBandChunks, yb = y0 + rows * (z + 1) / kBandChunks;
-  const float2 *o = obj + (size_t)t * n * n;
-  // a thread's few dozen samples in FP32 (FP64 arithmetic is slow on this part),
-  // the block's partials combined in FP64; the threads stride over the chunk's
-  // samples row after row, so narrow column bands keep every thread busy
-  float re = 0.f, im = 0.f;
-  const int width = x1 - x0, count = (yb - ya) * width;
-#pragma unroll 4
-  for (int i = (int)threadIdx.x; i < count; i += kBandThreads) {
-    const int y = ya + i / width, x = x0 + i % width;
-    const float2 v = o[(size_t)y * n + x];
-    re += v.x;
-    im += v.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = 0; b < 4; ++b) {
+    acc[b] = lanes_sum<32>(acc[b]);
+    if (lane == 0) part[warp][b] = acc[b];
   }
-  sre[threadIdx.x] = (double)re;
-  sim[threadIdx.x] = (double)im;
   __syncthreads();
-  for (int s = kBandThreads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sre[threadIdx.x] += sre[threadIdx.x + s];
-      sim[threadIdx.x] += sim[threadIdx.x + s];
+  if (threadIdx.x == 0) {
+    const float s1 = (float)(1.0 / n), s2 = (float)(1.0 / ((double)n * n));
+    for (int b = 0; b < 4; ++b) {
+      float2 v = part[0][b];
+      for (int q = 1; q < kWeightThreads / 32; ++q) v = cadd(v, part[q][b]);
+      const float sc = b < 2 ? s1 : s2;
+      sums[4 * t + b] = make_float2(v.x * sc, v.y * sc);
     }
-    __syncthreads();
+    __threadfence();
+    last = atomicAdd(counter, 1u) == (unsigned)ty - 1;
   }
-  if (threadIdx.x == 0) out[((size_t)t * 4 + band) * kBandChunks + z] = make_double2(sre[0], sim[0]);
-}
-
-// Tile (row or column) index of field-of-view line X: tile 0 up to
-// n - ov/2, then one tile per stride n - ov.
-__device__ __forceinline__ int tile_of_line(int x, int n, int ov, int k_tiles) {
-  if (x < n - ov / 2) return 0;
-  return min(k_tiles - 1, 1 + (x - (n - ov / 2)) / (n - ov));
-}
-
-// out[X][Y] = weight(i, j) * object(i, j)[X - i (n - ov)][Y - j (n - ov)]; rows X
-// strided over the grid, columns over the threads of a block.
-static __global__ void assemble_kernel(float2 *out, const float2 *obj, const float2 *weight, int n, int ov,
-                                       int tiles_y, int tiles_x, int fov_h, int fov_w) {
-  const int stride = n - ov;
-  for (int x = blockIdx.x; x < fov_h; x += gridDim.x) {
-    const int i = tile_of_line(x, n, ov, tiles_y);
-    const float2 *orow = obj + (size_t)i * tiles_x * n * n + (size_t)(x - i * stride) * n;
-    float2 *dst = out + (size_t)x * fov_w;
-    for (int y = threadIdx.x; y < fov_w; y += blockDim.x) {
-      const int j = tile_of_line(y, n, ov, tiles_x);
-      const float2 v = orow[(size_t)j * n * n + (y - j * stride)];
-      const float2 wt = weight[i * tiles_x + j];
-      dst[y] = make_float2(__fmaf_rn(wt.x, v.x, -__fmul_rn(wt.y, v.y)), __fmaf_rn(wt.x, v.y, __fmul_rn(wt.y, v.x)));
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  float2 *ss = chain_sm, *cs = chain_sm + 4 * ty;
+  for (int q = threadIdx.x; q < 4 * ty; q += kWeightThreads) ss[q] = __ldcg(sums + 4 * ((q >> 2) * tx + j) + (q & 3));
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const float2 zero = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f);
+  // c(r) = c(r-1) B(r-1) / T(r), or 1 where T(r) = 0
+  for (int r = lane; r < ty; r += 32) cs[r] = (r > 0 && cnonzero(ss[4 * r])) ? cdiv(ss[4 * (r - 1) + 1], ss[4 * r]) : one;
+  __syncwarp();
+  if (lane == 0) {
+    float2 c = one;
+    for (int r = 1; r < ty; ++r) {
+      c = cnonzero(ss[4 * r]) ? cmul(c, cs[r]) : one;
+      cs[r] = c;
     }
   }
+  __syncwarp();
+  float2 sl = zero, sr = zero;
+  for (int r = lane; r < ty; r += 32) {
+    sl = cadd(sl, cmul(cs[r], ss[4 * r + 2]));
+    sr = cadd(sr, cmul(cs[r], ss[4 * r + 3]));
+  }
+  sl = lanes_sum<32>(sl);
+  sr = lanes_sum<32>(sr);
+  float2 d = one;
+  if (j > 0 && cnonzero(sl)) d = cdiv(cmul(colst[0], colst[1]), sl);   // every lane: the same operands
+  __syncwarp();
+  if (lane == 0) {
+    colst[0] = d;
+    colst[1] = sr;
+  }
+  for (int r = lane; r < ty; r += 32) w[r * tx + j] = cmul(cs[r], d);
+  if (lane == 0) *counter = 0u;
 }
 
 }  // namespace fpm
@@ -172,43 +253,6 @@ static int check_device_error(fpm_plan *p, cudaStream_t st) {
   return FPM_OK;
 }
 
-// Per-tile weights of the stitched image from the band sums (see the top of the file).
-static std::vector<float2> stitch_weights(const StitchGeom &g, const std::vector<double2> &sums) {
-  using cd = std::complex<double>;
-  const int T = g.ty * g.tx;
-  std::vector<cd> c(T, cd(1.0, 0.0)), d(g.tx, cd(1.0, 0.0));
-  auto sum = [&](int t, int band) {
-    cd v(0.0, 0.0);
-    for (int z = 0; z < kBandChunks; ++z) {
-      const double2 c = sums[((size_t)t * 4 + band) * kBandChunks + z];
-      v += cd(c.x, c.y);
-    }
-    return v;
-  };
-  if (g.ov > 0) {
-    for (int j = 0; j < g.tx; ++j)
-      for (int i = 1; i < g.ty; ++i) {
-        const int t = i * g.tx + j, up = (i - 1) * g.tx + j;
-        const cd top = sum(t, 0);
-        c[t] = top != cd(0.0, 0.0) ? c[up] * sum(up, 1) / top : cd(1.0, 0.0);
-      }
-    for (int j = 1; j < g.tx; ++j) {
-      cd sl(0.0, 0.0), sr(0.0, 0.0);
-      for (int i = 0; i < g.ty; ++i) {
-        sl += c[i * g.tx + j] * sum(i * g.tx + j, 2);
-        sr += c[i * g.tx + j - 1] * sum(i * g.tx + j - 1, 3);
-      }
-      d[j] = sl != cd(0.0, 0.0) ? d[j - 1] * sr / sl : cd(1.0, 0.0);
-    }
-  }
-  std::vector<float2> w(T);
-  for (int t = 0; t < T; ++t) {
-    const cd v = c[t] * d[t % g.tx];
-    w[t] = make_float2((float)v.real(), (float)v.imag());
-  }
-  return w;
-}
-
 }  // namespace fpm
 
 using fpm::fail;
@@ -262,38 +306,62 @@ int fpm_stitch(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
   if (g.ov < 0 || 2 * g.ov > g.n)
     return fail(FPM_EINVAL, "HR overlap %d: stitching needs 0 <= overlap <= N/2 = %d", g.ov, g.n / 2);
   cudaStream_t st = (cudaStream_t)stream;
-  const int T = p->n_tiles;
-  const size_t nn = (size_t)g.n * g.n, fov = (size_t)g.fov_h * g.fov_w;
+  const int T = p->n_tiles, n = g.n;
+  const size_t nn = (size_t)n * n, fov = (size_t)g.fov_h * g.fov_w;
+  // one tile column at a time: its row transforms (8 B per sample) wait in buf,
+  // sized to stay in L2, until its weights are known
   Carve cv;
-  const size_t o_obj = cv.take<float2>((size_t)T * nn), o_tw = cv.take<float2>(g.n);
-  const size_t o_sums = cv.take<double2>((size_t)T * 4 * fpm::kBandChunks), o_w = cv.take<float2>(T);
+  const size_t o_buf = cv.take<float2>((size_t)g.ty * nn), o_band = cv.take<float2>((size_t)3 * g.ty * n);
+  const size_t o_sums = cv.take<float2>((size_t)4 * T), o_col = cv.take<float2>(2);
+  const size_t o_cnt = cv.take<unsigned>(1), o_w = cv.take<float2>(T);
   const size_t o_out = on_device ? 0 : cv.take<float2>(fov);
   void *base = nullptr;
   if ((rc = fpm::plan_scratch(p, cv.off, &base))) return rc;
   char *b = static_cast<char *>(base);
-  float2 *obj = reinterpret_cast<float2 *>(b + o_obj), *tw = reinterpret_cast<float2 *>(b + o_tw);
-  double2 *sums = reinterpret_cast<double2 *>(b + o_sums);
-  float2 *wdev = reinterpret_cast<float2 *>(b + o_w);
-  float2 *out = on_device ? static_cast<float2 *>(dst) : reinterpret_cast<float2 *>(b + o_out);
-  const std::vector<float2> twh = fpm::twiddles_line(g.n, +1);
-  if (cudaMemcpyAsync(tw, twh.data(), twh.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return fail(FPM_ECUDA, "fpm_stitch: table upload failed");
-  if ((rc = fpm::tile_objects(p, 0, T, obj, tw, st))) return rc;
-  std::vector<double2> sh((size_t)T * 4 * fpm::kBandChunks, make_double2(0.0, 0.0));
-  if (g.ov > 0) {
-    fpm::band_sums_kernel<<<dim3((unsigned)T, 4, fpm::kBandChunks), fpm::kBandThreads, 0, st>>>(obj, g.n, g.ov, g.ty,
-                                                                                                 g.tx, sums);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(sh.data(), sums, sh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return fail(FPM_ECUDA, "fpm_stitch: band sums failed");
+  auto at = [&](size_t off) { return reinterpret_cast<float2 *>(b + off); };
+  float2 *buf = at(o_buf), *band = at(o_band), *sums = at(o_sums), *w = at(o_w);
+  float2 *colst = at(o_col);
+  unsigned *counter = reinterpret_cast<unsigned *>(b + o_cnt);
+  float2 *out = on_device ? static_cast<float2 *>(dst) : at(o_out);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), st) != cudaSuccess)
+    return fail(FPM_ECUDA, "fpm_stitch: counter reset failed");
+  // the plan's tables: twiddles, twiddles in pass order and the band series
+  float2 **slot = fpm::plan_stitch_tables(p);
+  if (!slot) return fail(FPM_ESTATE, "fpm_stitch: no device state");
+  if (!*slot) {
+    const std::vector<float2> tab = fpm::stitch_tables(n, g.ov);
+    if (cudaMalloc((void **)slot, tab.size() * sizeof(float2)) != cudaSuccess) {
+      *slot = nullptr;
+      return fail(FPM_ENOMEM, "fpm_stitch: table allocation failed");
+    }
+    if (cudaMemcpy(*slot, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(FPM_ECUDA, "fpm_stitch: table upload failed");
   }
-  const std::vector<float2> w = fpm::stitch_weights(g, sh);
-  if (cudaMemcpyAsync(wdev, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return fail(FPM_ECUDA, "fpm_stitch: weight upload failed");
-  fpm::assemble_kernel<<<(unsigned)std::min(g.fov_h, 148 * 32), 256, 0, st>>>(out, obj, wdev, g.n, g.ov, g.ty, g.tx,
-                                                                             g.fov_h, g.fov_w);
-  if (cudaGetLastError() != cudaSuccess) return fail(FPM_ECUDA, "fpm_stitch: assembly launch failed");
+  const float2 *tw = *slot, *tw_pass = (n == 256 || n == 1024) ? *slot + n : nullptr;
+  const float2 *gt = *slot + n + fpm::kPassTab;
+  // the weights chain stages a tile column's sums and c values in shared memory
+  const size_t chain_smem = (size_t)g.ty * 5 * sizeof(float2);
+  if (chain_smem > 200 * 1024) return fail(FPM_EINVAL, "fpm_stitch: %d tile rows exceed the weight chain's limit", g.ty);
+  if (chain_smem > 48 * 1024 &&
+      cudaFuncSetAttribute((const void *)fpm::stitch_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)chain_smem) != cudaSuccess)
+    return fail(FPM_ECUDA, "fpm_stitch: weight kernel set-up failed");
+  // per tile column j: 1. row transforms of its spectra into buf, with each row's
+  // band values; 2. its band sums and weights (Eq. 1 chained down the column and
+  // from column j - 1); 3. column transforms writing weight x (-1)^(x+y) / N^2 x
+  // result into the image where the tile keeps the pixel
+  const float scale = (float)(1.0 / ((double)n * n));
+  for (int j = 0; j < g.tx; ++j) {
+    if ((rc = fpm::launch_fft_rows_banded(buf, fpm::plan_spectra(p) + (size_t)j * nn, tw, tw_pass, n, +1, g.ty,
+                                          (long long)g.tx * nn, band, g.ov, st)))
+      return rc;
+    fpm::stitch_weights_kernel<<<(unsigned)g.ty, fpm::kWeightThreads, chain_smem, st>>>(band, gt, n, g.ty, g.tx, j,
+                                                                                       sums, colst, counter, w);
+    if (cudaGetLastError() != cudaSuccess) return fail(FPM_ECUDA, "fpm_stitch: weight kernel failed to launch");
+    if ((rc = fpm::launch_fft_columns_to_fov(buf, tw, tw_pass, n, +1, g.ty, scale, out, w, g.fov_w, g.ov, g.ty, g.tx,
+                                             j, g.tx, st)))
+      return rc;
+  }
   if (!on_device && cudaMemcpyAsync(dst, out, fov * sizeof(float2), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail(FPM_ECUDA, "fpm_stitch: copy out failed");
   return on_device ? FPM_OK : fpm::check_device_error(p, st);
