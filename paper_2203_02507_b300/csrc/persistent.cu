@@ -45,7 +45,13 @@ struct PItem {
   int wave, target, width, ltile;  // target: tile's completed updates once this wave is done
 };
 
+// Jobs whose arguments travel inline in the kernel parameters (constant bank):
+// the update then reads them as the wave launches do, with no shared-memory
+// loads that its own shared-memory stores would force the compiler to repeat.
+constexpr int kInlineJobs = 16;
+
 struct PersistArgs {
+  JobArgs inl[kInlineJobs];        // the first jobs' arguments (all of them when INL)
   const JobArgs *jobs;
   const PItem *items;
   int n_items;
@@ -57,25 +63,32 @@ struct PersistArgs {
   long long timeout_ns;
 };
 
-// 2-CTA clusters of 384 threads for every tile side; a queue whose jobs all
-// have tiles of 256 runs 448 threads (14 warps, 144 registers each: the
-// column phase's 128 columns per CTA then take 5 rounds of 28 transforms).
-constexpr int kPC = 2, kPT = 384, kPT256 = 448;
+// 2-CTA clusters of 384 threads, one CTA per SM, for every tile side and for
+// mixed queues.  A queue whose jobs all have tiles of 256 runs the layout the
+// wave launches run: 4-CTA clusters of 256 threads (128 registers), two CTAs
+// of different clusters per SM, twiddles read through L1 and each column's
+// pixels fetched at the start of the column (8 registers fewer than one column
+// ahead, room for the queue loop's state).
+constexpr int kPC = 2, kPT = 384, kPC256 = 4, kPT256 = 256;
 using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1>;
 using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1>;
 using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1>;
 using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1>;
-using P256x = UpdateCfg<256, 16, 16, 16, kPC, kPT256, 1, 0>;
+using P256q = UpdateCfg<256, 16, 16, 16, kPC256, kPT256, 2, 0, 0, 1>;
 
 template <int MSEL>
 constexpr int persistent_threads() { return MSEL == 256 ? kPT256 : kPT; }
+template <int MSEL>
+constexpr int persistent_cluster() { return MSEL == 256 ? kPC256 : kPC; }
+template <int MSEL>
+constexpr int persistent_min_blocks() { return MSEL == 256 ? 2 : 1; }
 
 static size_t persistent_smem(int m, int rows, int msel) {
   switch (m) {
     case 64: return P64::smem_bytes(rows);
     case 128: return P128::smem_bytes(rows);
     case 192: return P192::smem_bytes(rows);
-    default: return msel == 256 ? P256x::smem_bytes(rows) : P256::smem_bytes(rows);
+    default: return msel == 256 ? P256q::smem_bytes(rows) : P256::smem_bytes(rows);
   }
 }
 
@@ -92,10 +105,28 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned *p) {
 __device__ __forceinline__ void store_release(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned add_acq_rel(unsigned *p, unsigned v) {
+__device__ __forceinline__ unsigned load_relaxed(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned add_relaxed(unsigned *p, unsigned v) {
   unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Count one finished update of entry `it` on its tile; true if it completes the
+// tile's wave.  The fence before orders the cluster's writes of the update (made
+// visible to this thread by the update's cluster barriers) before the count; the
+// fence after a completing count orders the other clusters' writes of the wave
+// before the merge that follows.
+__device__ __forceinline__ bool count_done(const PersistArgs &pa, const PItem &it) {
+  fence_acq_rel();
+  const bool last = add_relaxed(&pa.done[it.tile], 1u) + 1u == (unsigned)it.target;
+  if (last) fence_acq_rel();
+  return last;
 }
 
 // Wait until *flag >= want; false if the abort flag is raised or the time runs out.
@@ -113,20 +144,31 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
 
 // MSEL = 0: any tile side (dispatch per entry); MSEL = m: every job has tile side m,
 // so the kernel carries only that variant (and its register needs).
-template <typename Img, int MSEL>
-__global__ void __launch_bounds__(persistent_threads<MSEL>(), 1) persistent_kernel(const __grid_constant__ PersistArgs pa) {
+//
+// The queue work of an entry runs inside the update before it, on the thread of
+// the update's hook (cluster rank 0, last warp, which has a phase-3 row fewer
+// than the others): it counts the previous update done, claims the next entry,
+// reads it and looks whether its dependency is met.  The update's closing
+// barrier publishes the results, so in the common case (dependency met) the
+// next update starts with no barrier or wait of its own.  Otherwise the leader
+// takes the pending done count first (the entry may depend on the wave it
+// completes), merges if it completed a wave, and waits.
+template <typename Img, int MSEL, bool INL>
+__global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blocks<MSEL>())
+    persistent_kernel(const __grid_constant__ PersistArgs pa) {
+  constexpr int PC = persistent_cluster<MSEL>();
   extern __shared__ float4 smem_raw[];
-  // the cluster leader claims the next entry while the current one waits on its
-  // dependency and hands both to the cluster through these (entries double-
-  // buffered).  s_ok (dependency met) and s_last (wave completed) are separate:
-  // between a read of either and the leader's next write of it lies a cluster
-  // barrier inside the update.
-  __shared__ int s_idx[2], s_ok, s_last;
-  __shared__ PItem s_item[2];
+  // queue state, one copy per CTA written through distributed shared memory:
+  // a ring of three entries (current, next, previous, by position mod 3);
+  // s_ready: the next entry's dependency was seen met; s_last: the previous
+  // entry completed its tile's wave (from the hook); s_last0, s_ok: the same
+  // from the leader on the waiting path
+  __shared__ PItem s_item[3];
+  __shared__ int s_idx[3], s_ready, s_last, s_last0, s_ok;
   // the current job's arguments, read by the update from shared memory rather
   // than through a pointer into global memory
   __shared__ UpdateArgs s_args;
-  static_assert(sizeof(UpdateArgs) % 4 == 0 && sizeof(UpdateArgs) / 4 <= kPT, "one word per thread");
+  static_assert(sizeof(UpdateArgs) % 4 == 0 && sizeof(UpdateArgs) / 4 <= kPT256, "one word per thread");
   int args_job = -1;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned q = cl.block_rank();
@@ -136,87 +178,136 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), 1) persistent_kern
   if constexpr (MSEL == 64) load_twiddles<P64>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
   if constexpr (MSEL == 128) load_twiddles<P128>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
   if constexpr (MSEL == 192) load_twiddles<P192>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
-  if constexpr (MSEL == 256) load_twiddles<P256x>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
+  if constexpr (MSEL == 256) load_twiddles<P256q>(pa.jobs[0].u, reinterpret_cast<float2 *>(smem_raw));
   constexpr bool load_tw = MSEL == 0;   // mixed tile sides reload them per update
+  // every CTA of the cluster merges its share of a completed wave; the leader
+  // then releases the tile's next wave
+  auto merge_wave = [&](const PItem &it) {
+    const JobArgs *mj = pa.jobs + it.job;
+    if (mj->epry)
+      merge_rows(const_cast<float2 *>(mj->u.pup), mj->u.dpup, it.ltile, it.width, (int)q, PC, mj->u.y_lo,
+                 mj->u.rows, mj->m, mj->u.slots, mj->u.disc, threadIdx.x, blockDim.x);
+    __threadfence();
+    cl.sync();
+    if (leader) {
+      __threadfence();
+      store_release(&pa.merged[it.tile], (unsigned)it.wave + 1u);
+    }
+  };
   if (leader) {
     const int idx = (int)atomicAdd(pa.next, 1u);
     const PItem it = idx < pa.n_items ? pa.items[idx] : PItem{};
-    for (int r = 0; r < kPC; ++r) {
+    for (int r = 0; r < PC; ++r) {
       *cl.map_shared_rank(&s_idx[0], r) = idx;
       *cl.map_shared_rank(&s_item[0], r) = it;
     }
   }
   cl.sync();
-  for (int k = 0;; k ^= 1) {
-    if (s_idx[k] >= pa.n_items) break;
-    if (leader) {
-      const PItem it = s_item[k];
-      int nidx = (int)atomicAdd(pa.next, 1u);        // claim ahead; its latency overlaps the wait
-      const unsigned want = pa.stall_test ? 0xffffffffu : (unsigned)it.wave;
-      const bool ok = wait_for(&pa.merged[it.tile], want, &pa.err[1], pa.timeout_ns);
-      if (!ok) {
-        atomicOr(&pa.err[0], 1u);        // a dependency wait ran out (or another did)
-        atomicExch(&pa.err[1], 1u);
+  bool pending = false;   // the previous update is not counted done yet (uniform)
+  bool ready = false;     // the current entry's dependency was seen met (uniform)
+  bool aborted = false;   // a dependency wait ran out or another cluster aborted (uniform)
+  int k = 0;
+  for (;; k = (k + 1) % 3) {
+    const int cur = k, nxt = (k + 1) % 3, prv = (k + 2) % 3;
+    if (s_idx[cur] >= pa.n_items) break;
+    if (!ready) {
+      // the current entry may depend on the wave the previous update completes
+      if (pending) {
+        if (leader) {
+          const int last = count_done(pa, s_item[prv]) ? 1 : 0;
+          for (int r = 0; r < PC; ++r) *cl.map_shared_rank(&s_last0, r) = last;
+        }
+        cl.sync();
+        if (s_last0) merge_wave(s_item[prv]);
+        pending = false;
       }
-      if (load_acquire(&pa.err[1])) nidx = pa.n_items;
-      const PItem nit = nidx < pa.n_items ? pa.items[nidx] : PItem{};
-      for (int r = 0; r < kPC; ++r) {
-        *cl.map_shared_rank(&s_ok, r) = ok ? 1 : 0;
-        *cl.map_shared_rank(&s_idx[k ^ 1], r) = nidx;
-        *cl.map_shared_rank(&s_item[k ^ 1], r) = nit;
+      if (leader) {
+        const unsigned want = pa.stall_test ? 0xffffffffu : (unsigned)s_item[cur].wave;
+        const bool ok = wait_for(&pa.merged[s_item[cur].tile], want, &pa.err[1], pa.timeout_ns);
+        if (!ok) {
+          atomicOr(&pa.err[0], 1u);        // a dependency wait ran out (or another did)
+          atomicExch(&pa.err[1], 1u);
+        }
+        for (int r = 0; r < PC; ++r) *cl.map_shared_rank(&s_ok, r) = ok ? 1 : 0;
+      }
+      cl.sync();
+      if (!s_ok) {
+        aborted = true;
+        break;
       }
     }
-    cl.sync();
-    if (!s_ok) break;
-    // the item is re-read from shared memory after the update, so it does not
-    // stay in registers across it
-    const int job = s_item[k].job;
-    const JobArgs *jp = pa.jobs + job;
-    if (job != args_job) {                 // uniform: every thread read the same item
+    const int job = s_item[cur].job;
+    if (!INL && job != args_job) {         // uniform: every thread read the same entry
+      const JobArgs *jp = pa.jobs + job;
       if (threadIdx.x < sizeof(UpdateArgs) / 4)
         reinterpret_cast<unsigned *>(&s_args)[threadIdx.x] = reinterpret_cast<const unsigned *>(&jp->u)[threadIdx.x];
       args_job = job;
       __syncthreads();
     }
-    const int4 item = make_int4(s_item[k].ltile, s_item[k].led, s_item[k].slot, 0);
+    const int4 item = make_int4(s_item[cur].ltile, s_item[cur].led, s_item[cur].slot, 0);
+    const bool count_prev = pending;
+    unsigned h_done = 0;                   // the hook's requests, answered by its second stage
+    int h_nidx = 0;
+    auto hook = [&](int stage) {
+      if (stage == 0) {
+        // count the previous update done and claim the next entry; the answers
+        // arrive while this warp does its phase-3 rows
+        if (count_prev) {
+          fence_acq_rel();
+          h_done = add_relaxed(&pa.done[s_item[prv].tile], 1u);
+        }
+        h_nidx = (int)atomicAdd(pa.next, 1u);
+        return;
+      }
+      const int last = count_prev && h_done + 1u == (unsigned)s_item[prv].target ? 1 : 0;
+      if (last) fence_acq_rel();           // the wave's other writes, before this cluster merges it
+      const int nidx = load_relaxed(&pa.err[1]) ? pa.n_items : h_nidx;
+      const PItem nit = nidx < pa.n_items ? pa.items[nidx] : PItem{};
+      int rdy = 0;
+      if (nidx < pa.n_items && !pa.stall_test) {
+        const unsigned mg = load_relaxed(&pa.merged[nit.tile]), ab = load_relaxed(&pa.err[1]);
+        rdy = (mg >= (unsigned)nit.wave && !ab) ? 1 : 0;
+        if (rdy) fence_acq_rel();          // the merge that released it, before the next update reads
+      }
+      for (int r = 0; r < PC; ++r) {
+        *cl.map_shared_rank(&s_idx[nxt], r) = nidx;
+        *cl.map_shared_rank(&s_item[nxt], r) = nit;
+        *cl.map_shared_rank(&s_last, r) = last;
+        *cl.map_shared_rank(&s_ready, r) = rdy;
+      }
+    };
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    const UpdateArgs &ua = INL ? pa.inl[job].u : s_args;
     if constexpr (MSEL == 64) {
-      run_update<P64, Img>(s_args, item, smem, load_tw);
+      run_update<P64, Img>(ua, item, smem, load_tw, true, hook);
     } else if constexpr (MSEL == 128) {
-      run_update<P128, Img>(s_args, item, smem, load_tw);
+      run_update<P128, Img>(ua, item, smem, load_tw, true, hook);
     } else if constexpr (MSEL == 192) {
-      run_update<P192, Img>(s_args, item, smem, load_tw);
+      run_update<P192, Img>(ua, item, smem, load_tw, true, hook);
     } else if constexpr (MSEL == 256) {
-      run_update<P256x, Img>(s_args, item, smem, load_tw);
+      run_update<P256q, Img>(ua, item, smem, load_tw, true, hook);
     } else {
-      switch (jp->m) {
-        case 64: run_update<P64, Img>(s_args, item, smem, load_tw); break;
-        case 128: run_update<P128, Img>(s_args, item, smem, load_tw); break;
-        case 192: run_update<P192, Img>(s_args, item, smem, load_tw); break;
-        default: run_update<P256, Img>(s_args, item, smem, load_tw); break;
+      switch (INL ? pa.inl[job].m : pa.jobs[job].m) {
+        case 64: run_update<P64, Img>(ua, item, smem, load_tw, true, hook); break;
+        case 128: run_update<P128, Img>(ua, item, smem, load_tw, true, hook); break;
+        case 192: run_update<P192, Img>(ua, item, smem, load_tw, true, hook); break;
+        default: run_update<P256, Img>(ua, item, smem, load_tw, true, hook); break;
       }
     }
-    const PItem done_it = s_item[k];
-    // run_update ends with a cluster barrier: all of this update's writes are issued
+    // the update's closing cluster barrier published the hook's results
+    if (s_last) merge_wave(s_item[prv]);
+    ready = s_ready != 0;
+    pending = true;
+  }
+  // the last update's done count, and its wave's merge (not after an abort)
+  if (pending && !aborted) {
+    const int prv = (k + 2) % 3;
     if (leader) {
-      __threadfence();
-      const unsigned old = add_acq_rel(&pa.done[done_it.tile], 1u);
-      const int last = (old + 1u == (unsigned)done_it.target) ? 1 : 0;
-      for (int r = 0; r < kPC; ++r) *cl.map_shared_rank(&s_last, r) = last;
+      const int last = count_done(pa, s_item[prv]) ? 1 : 0;
+      for (int r = 0; r < PC; ++r) *cl.map_shared_rank(&s_last0, r) = last;
     }
     cl.sync();
-    if (s_last) {          // this cluster completed the tile's wave: merge it, release the next
-      const JobArgs *mj = pa.jobs + done_it.job;
-      if (mj->epry)
-        merge_rows(const_cast<float2 *>(mj->u.pup), mj->u.dpup, done_it.ltile, done_it.width, (int)q, kPC,
-                   mj->u.y_lo, mj->u.rows, mj->m, mj->u.slots, mj->u.disc, threadIdx.x, blockDim.x);
-      __threadfence();
-      cl.sync();
-      if (leader) {
-        __threadfence();
-        store_release(&pa.merged[done_it.tile], (unsigned)done_it.wave + 1u);
-      }
-    }
+    if (s_last0) merge_wave(s_item[prv]);
   }
 }
 
@@ -278,6 +369,7 @@ struct QueueDev {
   size_t smem = 0;
   int dtype = FPM_U16;
   int msel = 0;                   // common tile side of the jobs, 0 if mixed
+  std::vector<JobArgs> host_jobs; // the job table (the first kInlineJobs go inline)
 };
 
 void free_queue(QueueDev *q) {
@@ -329,6 +421,7 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
   if ((rc = grow(&q->counters, &q->cap_tiles, 1 + 2 * (size_t)tiles))) return rc;
   if (n_items) FPM_CK(cudaMemcpyAsync(q->items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
   FPM_CK(cudaMemcpyAsync(q->jobs, ja.data(), ja.size() * sizeof(JobArgs), cudaMemcpyHostToDevice, st));
+  q->host_jobs = ja;
   q->n_items = (int)n_items;
   q->n_tiles = tiles;
   q->n_jobs = (int)jobs.size();
@@ -359,13 +452,13 @@ int persistent_block_threads(int m) { return m == 256 ? kPT256 : kPT; }
 bool persistent_fits(int m, int rows) {
   return std::max(persistent_smem(m, rows, m), persistent_smem(m, rows, 0)) <= 232448;
 }
-int persistent_cluster_size(int) { return kPC; }
+int persistent_cluster_size(int m) { return m == 256 ? kPC256 : kPC; }
 int persistent_lanes(int m) {
   switch (m) {
     case 64: return P64::TPT;
     case 128: return P128::TPT;
     case 192: return P192::TPT;
-    default: return P256x::TPT;
+    default: return P256q::TPT;
   }
 }
 
@@ -374,6 +467,7 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   FPM_CK(cudaMemsetAsync(q->counters, 0, (1 + 2 * (size_t)q->n_tiles) * 4, st));
   FPM_CK(cudaMemsetAsync(err, 0, 2 * sizeof(unsigned), st));
   PersistArgs pa{};
+  for (int j = 0; j < std::min(q->n_jobs, kInlineJobs); ++j) pa.inl[j] = q->host_jobs[j];
   pa.jobs = q->jobs;
   pa.items = q->items;
   pa.n_items = q->n_items;
@@ -386,13 +480,19 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   using K = void (*)(PersistArgs);
   const bool u16 = q->dtype == FPM_U16;
   K k;
+  // at most kInlineJobs jobs: their arguments from the kernel parameters
+  const bool inl = q->n_jobs <= kInlineJobs;
+#define FPM_PK(M) \
+  (u16 ? (inl ? (K)&persistent_kernel<uint16_t, M, true> : (K)&persistent_kernel<uint16_t, M, false>) \
+       : (inl ? (K)&persistent_kernel<float, M, true> : (K)&persistent_kernel<float, M, false>))
   switch (q->msel) {
-    case 64: k = u16 ? (K)&persistent_kernel<uint16_t, 64> : (K)&persistent_kernel<float, 64>; break;
-    case 128: k = u16 ? (K)&persistent_kernel<uint16_t, 128> : (K)&persistent_kernel<float, 128>; break;
-    case 192: k = u16 ? (K)&persistent_kernel<uint16_t, 192> : (K)&persistent_kernel<float, 192>; break;
-    case 256: k = u16 ? (K)&persistent_kernel<uint16_t, 256> : (K)&persistent_kernel<float, 256>; break;
-    default: k = u16 ? (K)&persistent_kernel<uint16_t, 0> : (K)&persistent_kernel<float, 0>; break;
+    case 64: k = FPM_PK(64); break;
+    case 128: k = FPM_PK(128); break;
+    case 192: k = FPM_PK(192); break;
+    case 256: k = FPM_PK(256); break;
+    default: k = FPM_PK(0); break;
   }
+#undef FPM_PK
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));
   cudaLaunchConfig_t cfg{};
   cfg.blockDim = dim3(persistent_block_threads(q->msel), 1, 1);
@@ -400,17 +500,18 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kPC;
+  const int pc = persistent_cluster_size(q->msel);
+  attr[0].val.clusterDim.x = (unsigned)pc;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3(kPC, 1, 1);
+  cfg.gridDim = dim3((unsigned)pc, 1, 1);
   int clusters = 0;
   FPM_CK(cudaOccupancyMaxActiveClusters(&clusters, (void *)k, &cfg));
   if (clusters < 1) return fail(FPM_EINVAL, "the persistent kernel does not fit on this device");
   clusters = std::min(clusters, std::max(1, q->n_items));
-  cfg.gridDim = dim3((unsigned)(clusters * kPC), 1, 1);
+  cfg.gridDim = dim3((unsigned)(clusters * pc), 1, 1);
   FPM_CK(cudaLaunchKernelEx(&cfg, k, pa));
   if (clusters_out) *clusters_out = clusters;
   return FPM_OK;

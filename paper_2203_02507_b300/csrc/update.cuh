@@ -29,6 +29,7 @@
 
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "aux_kernels.cuh"
 #include "dft.cuh"
@@ -130,6 +131,11 @@ __device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem)
   }
 }
 
+// No work at the hook point of run_update.
+struct NoHook {
+  __device__ __forceinline__ void operator()(int) const {}
+};
+
 // One update; all threads of all C CTAs of the cluster call this with the same item.
 // Shared memory: [twiddles 2m (not with Cfg::TG)][normaliser partials][inter R x W][exchange scratch].
 // load_tw = false keeps the twiddles of an earlier update with the same m.
@@ -137,9 +143,14 @@ __device__ __forceinline__ void load_twiddles(const UpdateArgs &a, float2 *smem)
 // writes before whatever the cluster does next (the persistent kernel signals
 // completion right after); false: the barrier only keeps the CTAs' shared memory
 // alive until the cluster has read it, and the kernel's end orders the writes.
-template <class Cfg, typename Img>
+// hook(0) and hook(1) run on one thread (cluster rank 0, the first lane of the
+// last warp, whose groups have the fewest phase-3 rows): hook(0) before its
+// phase-3 rows (for requests whose answers it needs only later), hook(1) after
+// them and before the closing barrier, which publishes what it writes to shared
+// memory.
+template <class Cfg, typename Img, class Hook = NoHook>
 __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float2 *smem, bool load_tw = true,
-                                           bool ordered_end = true) {
+                                           bool ordered_end = true, const Hook &hook = Hook{}) {
   constexpr int M = Cfg::M, A = Cfg::A, B = Cfg::B, TPT = Cfg::TPT, C = Cfg::C, T = Cfg::T;
   constexpr int W = Cfg::W, G = Cfg::G, SCR = Cfg::SCR;
   const int rows = a.rows;
@@ -423,6 +434,10 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const float inv_pn = 1.f / pn;
 
   // ---- phase 3: DFT along x of the support rows, then the updates ----------
+  constexpr bool kHook = !std::is_same<Hook, NoHook>::value;
+  if constexpr (kHook) {
+    if (q == 0 && tid == T - 32) hook(0);
+  }
   for (int i = r0 + g; i < r1; i += G) {
     const int by = a.y_lo + i;
     const int2 ch = a.chords[by];
@@ -486,6 +501,10 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
       }
     }
     __syncwarp(gmask);
+  }
+  if constexpr (kHook) {
+    if (q == 0 && tid == T - 32) hook(1);
+    __syncwarp();
   }
   // keep this CTA's shared memory alive until the cluster is done reading it
   if constexpr (C > 1) {
