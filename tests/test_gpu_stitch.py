@@ -23,6 +23,9 @@ SMALL = [
                    defocus_um=(-20.0, 20.0), seed_offset=9100),
     synth.Workload("st128", sensor=256, tile=128, tiles=2, overlap=16, iters=1, epry=True, optics=O9,
                    defocus_um=(-20.0, 20.0), seed_offset=9200),
+    # N = 768: the general line FFT (a radix-3 pass) with the row pass's band sums
+    synth.Workload("st192", sensor=384, tile=192, tiles=2, overlap=16, iters=1, epry=True, optics=O9,
+                   defocus_um=(-20.0, 20.0), seed_offset=9300),
 ]
 
 
