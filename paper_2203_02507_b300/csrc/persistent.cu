@@ -67,14 +67,16 @@ struct PersistArgs {
 // mixed queues.  A queue whose jobs all have tiles of 256 runs the layout the
 // wave launches run: 4-CTA clusters of 256 threads (128 registers), two CTAs
 // of different clusters per SM, twiddles read through L1 and each column's
-// pixels fetched at the start of the column (8 registers fewer than one column
-// ahead, room for the queue loop's state).
+// pixels fetched one column ahead.  The persistent configurations reach the
+// other CTAs' shared memory through generic pointers (DS = 0): with the queue
+// loop's state around the update, the explicit shared::cluster accesses cost
+// spills.
 constexpr int kPC = 2, kPT = 384, kPC256 = 4, kPT256 = 256;
-using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1>;
-using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1>;
-using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1>;
-using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1>;
-using P256q = UpdateCfg<256, 16, 16, 16, kPC256, kPT256, 2, 0, 0, 1>;
+using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1, 1, 0, 0, 0>;
+using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1, 1, 0, 0, 0>;
+using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1, 1, 0, 0, 0>;
+using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1, 1, 0, 0, 0>;
+using P256q = UpdateCfg<256, 16, 16, 16, kPC256, kPT256, 2, 1, 0, 1, 0>;
 
 template <int MSEL>
 constexpr int persistent_threads() { return MSEL == 256 ? kPT256 : kPT; }
@@ -153,7 +155,12 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
 // next update starts with no barrier or wait of its own.  Otherwise the leader
 // takes the pending done count first (the entry may depend on the wave it
 // completes), merges if it completed a wave, and waits.
-template <typename Img, int MSEL, bool INL>
+// INL = 0: the jobs' arguments are read from the table in global memory (copied
+// into shared memory when the job changes); 1: from the inline table in the
+// kernel parameters, indexed by the entry's job; 2: one job, whose arguments are
+// the inline table's first entry at a constant offset (the update then reads
+// them as immediate constant-bank operands, as in the wave launches).
+template <typename Img, int MSEL, int INL>
 __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blocks<MSEL>())
     persistent_kernel(const __grid_constant__ PersistArgs pa) {
   constexpr int PC = persistent_cluster<MSEL>();
@@ -187,7 +194,8 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     if (mj->epry)
       merge_rows(const_cast<float2 *>(mj->u.pup), mj->u.dpup, it.ltile, it.width, (int)q, PC, mj->u.y_lo,
                  mj->u.rows, mj->m, mj->u.slots, mj->u.disc, threadIdx.x, blockDim.x);
-    __threadfence();
+    // the cluster barrier orders every thread's pupil writes before the leader's
+    // fence, which orders them (cumulatively) before the release of the wave
     cl.sync();
     if (leader) {
       __threadfence();
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
       }
     }
     const int job = s_item[cur].job;
-    if (!INL && job != args_job) {         // uniform: every thread read the same entry
+    if (INL == 0 && job != args_job) {         // uniform: every thread read the same entry
       const JobArgs *jp = pa.jobs + job;
       if (threadIdx.x < sizeof(UpdateArgs) / 4)
         reinterpret_cast<unsigned *>(&s_args)[threadIdx.x] = reinterpret_cast<const unsigned *>(&jp->u)[threadIdx.x];
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
       }
     };
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
-    const UpdateArgs &ua = INL ? pa.inl[job].u : s_args;
+    const UpdateArgs &ua = INL == 2 ? pa.inl[0].u : INL == 1 ? pa.inl[job].u : s_args;
     if constexpr (MSEL == 64) {
       run_update<P64, Img>(ua, item, smem, load_tw, true, hook);
     } else if constexpr (MSEL == 128) {
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     } else if constexpr (MSEL == 256) {
       run_update<P256q, Img>(ua, item, smem, load_tw, true, hook);
     } else {
-      switch (INL ? pa.inl[job].m : pa.jobs[job].m) {
+      switch (INL ? pa.inl[INL == 2 ? 0 : job].m : pa.jobs[job].m) {
         case 64: run_update<P64, Img>(ua, item, smem, load_tw, true, hook); break;
         case 128: run_update<P128, Img>(ua, item, smem, load_tw, true, hook); break;
         case 192: run_update<P192, Img>(ua, item, smem, load_tw, true, hook); break;
@@ -480,11 +488,14 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   using K = void (*)(PersistArgs);
   const bool u16 = q->dtype == FPM_U16;
   K k;
-  // at most kInlineJobs jobs: their arguments from the kernel parameters
-  const bool inl = q->n_jobs <= kInlineJobs;
-#define FPM_PK(M) \
-  (u16 ? (inl ? (K)&persistent_kernel<uint16_t, M, true> : (K)&persistent_kernel<uint16_t, M, false>) \
-       : (inl ? (K)&persistent_kernel<float, M, true> : (K)&persistent_kernel<float, M, false>))
+  // at most kInlineJobs jobs: their arguments from the kernel parameters (one job:
+  // at constant offsets)
+  const int inl = q->n_jobs == 1 ? 2 : q->n_jobs <= kInlineJobs ? 1 : 0;
+#define FPM_PK(M)                                                                                      \
+  (u16 ? (inl == 2 ? (K)&persistent_kernel<uint16_t, M, 2>                                             \
+                   : inl ? (K)&persistent_kernel<uint16_t, M, 1> : (K)&persistent_kernel<uint16_t, M, 0>) \
+       : (inl == 2 ? (K)&persistent_kernel<float, M, 2>                                                \
+                   : inl ? (K)&persistent_kernel<float, M, 1> : (K)&persistent_kernel<float, M, 0>))
   switch (q->msel) {
     case 64: k = FPM_PK(64); break;
     case 128: k = FPM_PK(128); break;

@@ -48,6 +48,22 @@ namespace fpm {
 __device__ __forceinline__ int inter_swz(int y, int p) { return p ^ ((y ^ (p >> 4)) & 15); }
 __device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz(y, p); }
 
+// Accesses to a cluster CTA's shared memory through its 32-bit shared::cluster
+// address (mapa), not through a generic pointer.
+__device__ __forceinline__ uint32_t cluster_addr(const void *local_smem, int rank) {
+  uint32_t r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local_smem)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+
 // B consecutive image elements of one column (one lane's pixels in the column
 // phase), fetched with 16-byte loads and kept packed until they are used.
 template <typename Img, int B>
@@ -93,10 +109,15 @@ struct ImgCol {
 // the second pass of the current row (4 A registers more); 0: at the row's start.
 // TG_ = 1: the twiddles are read from global memory (they stay in L1) instead of
 // shared memory, 4 KB less shared memory per CTA at m = 256.
-template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0, int TG_ = 0>
+// DS_ = 1: the other CTAs' "inter" is accessed through 32-bit shared::cluster
+// addresses (mapa); 0: through generic pointers (map_shared_rank), which leaves
+// the register allocator more freedom where the update is inlined into a loop
+// with state of its own (the persistent kernel).
+template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0, int TG_ = 0,
+          int DS_ = 1>
 struct UpdateCfg {
   static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_, PR = PR_;
-  static constexpr int TG = TG_;
+  static constexpr int TG = TG_, DS = DS_;
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -169,11 +190,15 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 
   int q = 0;
   float2 *inter_of[C];
+  uint32_t inter_cl[C];                     // shared::cluster addresses of the CTAs' inter
   if constexpr (C > 1) {
     cg::cluster_group cl = cg::this_cluster();
     q = (int)cl.block_rank();
 #pragma unroll
-    for (int r = 0; r < C; ++r) inter_of[r] = cl.map_shared_rank(inter, r);
+    for (int r = 0; r < C; ++r) {
+      if constexpr (Cfg::DS) inter_cl[r] = cluster_addr(inter, r);
+      else inter_of[r] = cl.map_shared_rank(inter, r);
+    }
   } else {
     inter_of[0] = inter;
   }
@@ -270,7 +295,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = k1 + A * k2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          inter_of[owner][inter_at(i, by, p, W)] = v[k2];
+          if constexpr (C > 1 && Cfg::DS) st_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at(i, by, p, W), v[k2]);
+          else inter_of[owner][inter_at(i, by, p, W)] = v[k2];
         }
       }
     }
@@ -466,7 +492,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = A * aa + b2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          v[aa] = inter_of[owner][inter_at(i, by, p, W)];
+          if constexpr (C > 1 && Cfg::DS) v[aa] = ld_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at(i, by, p, W));
+          else v[aa] = inter_of[owner][inter_at(i, by, p, W)];
         }
         Dft<B, -1>::run(v);
 #pragma unroll
