@@ -444,8 +444,9 @@ def stitch_timing(plan, torch, dev, stack, k, w, reps=3):
             "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_peak_gbs": peak, "frac": gbs / peak, "peak_source": src,
             "includes": "one tile column at a time: row transforms of its spectra (with each row's band values), "
                         "its band sums and Eq. 1 weights on the device, column transforms writing weight x object "
-                        "straight into the image; the row transforms' output waits in L2; scratch kept with the "
-                        "plan"}
+                        "straight into the image; two row buffers, so the next column's row transforms run "
+                        "while this column's weights and column transforms run on a second stream; scratch "
+                        "kept with the plan"}
 
 
 def uneven_batch(torch, dev, steps=3):

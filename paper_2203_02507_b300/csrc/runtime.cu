@@ -229,6 +229,8 @@ struct DeviceState {
   cudaEvent_t branch_ev[2 * kMaxBranches] = {};
   cudaStream_t batch_st = nullptr;                 // this plan's part of a wave-mode batch
   cudaEvent_t batch_ev[2] = {};
+  cudaStream_t stitch_st = nullptr;                // the stitch's second stream and its events
+  cudaEvent_t stitch_ev[kStitchEvents] = {};
 };
 
 static void dfree(void *p) {
@@ -253,6 +255,9 @@ void destroy_device_state(fpm_plan *p) {
     if (ev) cudaEventDestroy(ev);
   if (d->batch_st) cudaStreamDestroy(d->batch_st);
   for (cudaEvent_t ev : d->batch_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (d->stitch_st) cudaStreamDestroy(d->stitch_st);
+  for (cudaEvent_t ev : d->stitch_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto &kv : d->queues) free_queue(kv.second);
   forget_batches(p);
@@ -616,6 +621,23 @@ unsigned *plan_error_word(fpm_plan *p) { return p->dev ? p->dev->err : nullptr; 
 
 const float2 *plan_spectra(const fpm_plan *p) { return (p->dev && p->dev->loaded) ? p->dev->spec : nullptr; }
 float2 **plan_stitch_tables(fpm_plan *p) { return p->dev ? &p->dev->stitch_tab : nullptr; }
+
+int plan_stitch_streams(fpm_plan *p, cudaStream_t *aux, cudaEvent_t **ev) {
+  DeviceState *d = p->dev;
+  if (!d) return fail(FPM_ESTATE, "no device state before fpm_load_tiles");
+  if (!d->stitch_st) {
+    if (cudaStreamCreateWithFlags(&d->stitch_st, cudaStreamNonBlocking) != cudaSuccess) {
+      d->stitch_st = nullptr;
+      return fail(FPM_ECUDA, "stitch stream creation failed");
+    }
+    for (cudaEvent_t &e : d->stitch_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return fail(FPM_ECUDA, "stitch event creation failed");
+  }
+  *aux = d->stitch_st;
+  *ev = d->stitch_ev;
+  return FPM_OK;
+}
 
 int plan_scratch(fpm_plan *p, size_t bytes, void **out) {
   DeviceState *d = p->dev;

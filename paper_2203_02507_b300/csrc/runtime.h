@@ -93,6 +93,10 @@ const float2 *plan_spectra(const fpm_plan *p);
 // Slot of the plan's stitch tables (device memory freed with the plan; null
 // until the first stitch builds them), or null without device state.
 float2 **plan_stitch_tables(fpm_plan *p);
+// The plan's second stream for the stitch and its kStitchEvents events (made on
+// first use, destroyed with the plan).
+constexpr int kStitchEvents = 5;
+int plan_stitch_streams(fpm_plan *p, cudaStream_t *aux, cudaEvent_t **ev);
 // A device scratch buffer of at least `bytes`, kept with the plan (grown on
 // demand, freed with the plan); its contents do not survive the next call.
 int plan_scratch(fpm_plan *p, size_t bytes, void **out);

@@ -30,11 +30,14 @@
 // as they store, and the sums over ky with the closed-form g take a few
 // thousand terms per tile.  Weight c(i,j) needs only tiles above (i,j) and d(j)
 // only columns up to j, so the tiles go one tile column at a time: row
-// transforms into a buffer the size of one tile column (kept in L2: the spectra
-// are read and the image written with evict-first hints), the column's weights
-// on the device, then the column transforms write weight x object straight into
-// the stitched image, only where the tile keeps the pixel.  Every spectrum is
-// read once and every image pixel written once; no host round trip.
+// transforms into a buffer the size of one tile column (the spectra are read and
+// the image written with evict-first hints, so the buffer's lines stay in L2),
+// the column's weights on the device, then the column transforms write weight x
+// object straight into the stitched image, only where the tile keeps the pixel.
+// Two such buffers let the row transforms of column j + 1 run on the caller's
+// stream while the weights and column transforms of column j run on a second
+// one.  Every spectrum is read once and every image pixel written once; no host
+// round trip.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -308,10 +311,12 @@ int fpm_stitch(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int T = p->n_tiles, n = g.n;
   const size_t nn = (size_t)n * n, fov = (size_t)g.fov_h * g.fov_w;
-  // one tile column at a time: its row transforms (8 B per sample) wait in buf,
-  // sized to stay in L2, until its weights are known
+  // one tile column at a time: its row transforms (8 B per sample) wait in a
+  // buffer of one tile column until its weights are known; two buffers, so that
+  // the next column's row transforms run while this column's weights and
+  // column transforms do (on the plan's second stream)
   Carve cv;
-  const size_t o_buf = cv.take<float2>((size_t)g.ty * nn), o_band = cv.take<float2>((size_t)3 * g.ty * n);
+  const size_t o_buf = cv.take<float2>((size_t)2 * g.ty * nn), o_band = cv.take<float2>((size_t)2 * 3 * g.ty * n);
   const size_t o_sums = cv.take<float2>((size_t)4 * T), o_col = cv.take<float2>(2);
   const size_t o_cnt = cv.take<unsigned>(1), o_w = cv.take<float2>(T);
   const size_t o_out = on_device ? 0 : cv.take<float2>(fov);
@@ -319,7 +324,9 @@ int fpm_stitch(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
   if ((rc = fpm::plan_scratch(p, cv.off, &base))) return rc;
   char *b = static_cast<char *>(base);
   auto at = [&](size_t off) { return reinterpret_cast<float2 *>(b + off); };
-  float2 *buf = at(o_buf), *band = at(o_band), *sums = at(o_sums), *w = at(o_w);
+  float2 *buf2[2] = {at(o_buf), at(o_buf) + (size_t)g.ty * nn};
+  float2 *band2[2] = {at(o_band), at(o_band) + (size_t)3 * g.ty * n};
+  float2 *sums = at(o_sums), *w = at(o_w);
   float2 *colst = at(o_col);
   unsigned *counter = reinterpret_cast<unsigned *>(b + o_cnt);
   float2 *out = on_device ? static_cast<float2 *>(dst) : at(o_out);
@@ -346,22 +353,39 @@ int fpm_stitch(fpm_plan *p, void *dst, int32_t on_device, void *stream) {
       cudaFuncSetAttribute((const void *)fpm::stitch_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)chain_smem) != cudaSuccess)
     return fail(FPM_ECUDA, "fpm_stitch: weight kernel set-up failed");
-  // per tile column j: 1. row transforms of its spectra into buf, with each row's
-  // band values; 2. its band sums and weights (Eq. 1 chained down the column and
-  // from column j - 1); 3. column transforms writing weight x (-1)^(x+y) / N^2 x
-  // result into the image where the tile keeps the pixel
+  // per tile column j: 1. (stream st) row transforms of its spectra into buffer
+  // j mod 2, with each row's band values; 2. (second stream) its band sums and
+  // weights (Eq. 1 chained down the column and from column j - 1); 3. (second
+  // stream) column transforms writing weight x (-1)^(x+y) / N^2 x result into the
+  // image where the tile keeps the pixel.  Events order 2 after 1 and the row
+  // transforms of column j + 2 after the column transforms of column j (same
+  // buffer); the second stream starts after and ends before st's work.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t *ev = nullptr;   // [0] fork, [1 + b] rows done in buffer b, [3 + b] buffer b free
+  if ((rc = fpm::plan_stitch_streams(p, &aux, &ev))) return rc;
+  auto ck = [&](cudaError_t e, const char *what) { return e == cudaSuccess ? FPM_OK : fail(FPM_ECUDA, "fpm_stitch: %s", what); };
+  if ((rc = ck(cudaEventRecord(ev[0], st), "fork")) || (rc = ck(cudaStreamWaitEvent(aux, ev[0], 0), "fork")))
+    return rc;
   const float scale = (float)(1.0 / ((double)n * n));
   for (int j = 0; j < g.tx; ++j) {
-    if ((rc = fpm::launch_fft_rows_banded(buf, fpm::plan_spectra(p) + (size_t)j * nn, tw, tw_pass, n, +1, g.ty,
-                                          (long long)g.tx * nn, band, g.ov, st)))
+    const int bsel = j & 1;
+    if (j >= 2 && (rc = ck(cudaStreamWaitEvent(st, ev[3 + bsel], 0), "buffer wait"))) return rc;
+    if ((rc = fpm::launch_fft_rows_banded(buf2[bsel], fpm::plan_spectra(p) + (size_t)j * nn, tw, tw_pass, n, +1,
+                                          g.ty, (long long)g.tx * nn, band2[bsel], g.ov, st)))
       return rc;
-    fpm::stitch_weights_kernel<<<(unsigned)g.ty, fpm::kWeightThreads, chain_smem, st>>>(band, gt, n, g.ty, g.tx, j,
-                                                                                       sums, colst, counter, w);
+    if ((rc = ck(cudaEventRecord(ev[1 + bsel], st), "rows event")) ||
+        (rc = ck(cudaStreamWaitEvent(aux, ev[1 + bsel], 0), "rows wait")))
+      return rc;
+    fpm::stitch_weights_kernel<<<(unsigned)g.ty, fpm::kWeightThreads, chain_smem, aux>>>(band2[bsel], gt, n, g.ty,
+                                                                                        g.tx, j, sums, colst, counter, w);
     if (cudaGetLastError() != cudaSuccess) return fail(FPM_ECUDA, "fpm_stitch: weight kernel failed to launch");
-    if ((rc = fpm::launch_fft_columns_to_fov(buf, tw, tw_pass, n, +1, g.ty, scale, out, w, g.fov_w, g.ov, g.ty, g.tx,
-                                             j, g.tx, st)))
+    if ((rc = fpm::launch_fft_columns_to_fov(buf2[bsel], tw, tw_pass, n, +1, g.ty, scale, out, w, g.fov_w, g.ov, g.ty,
+                                             g.tx, j, g.tx, aux)))
       return rc;
+    if ((rc = ck(cudaEventRecord(ev[3 + bsel], aux), "columns event"))) return rc;
   }
+  // join: st continues after the last column transforms
+  if ((rc = ck(cudaStreamWaitEvent(st, ev[3 + ((g.tx - 1) & 1)], 0), "join"))) return rc;
   if (!on_device && cudaMemcpyAsync(dst, out, fov * sizeof(float2), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail(FPM_ECUDA, "fpm_stitch: copy out failed");
   return on_device ? FPM_OK : fpm::check_device_error(p, st);
