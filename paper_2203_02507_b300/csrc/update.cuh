@@ -95,11 +95,11 @@ struct ImgCol {
       return __uint_as_float(w[k]);
     }
   }
-  // the measured intensity of pixel k: counts times 1/counts_per_unit, negative
-  // values clamped to zero (16-bit counts are never negative)
-  __device__ __forceinline__ float intensity(int k, float inv_counts) const {
-    if constexpr (sizeof(Img) == 2) return __fmul_rn(get(k), inv_counts);
-    else return fmaxf(__fmul_rn(get(k), inv_counts), 0.f);
+  // the measured counts of pixel k (intensity = counts / counts_per_unit),
+  // negative values clamped to zero (16-bit counts are never negative)
+  __device__ __forceinline__ float counts(int k) const {
+    if constexpr (sizeof(Img) == 2) return get(k);
+    else return fmaxf(get(k), 0.f);
   }
 };
 
@@ -393,27 +393,30 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
         for (int bb = 0; bb < B; ++bb) v[bb] = scr[bb * (A + 1) + k1];
         Dft<B, 1>::run(v);
-        // amplitude step at y = k1 + A k2, without branches: sqrt(I) / |phi~| =
-        // I / sqrt(I |phi~|^2) with the hardware reciprocal square root (a couple of
-        // ulp; a Newton-Raphson refinement cost 2% of the update and moved the
-        // parity errors by less than their float32 floor).  x is held at FLT_MIN or
-        // above, so I = 0 gives 0 * (finite r) = 0 with no select.  Pixels with
-        // phi~ = 0 (rare) are flagged and take sqrt(I) afterwards.
-        unsigned zmask = 0;
+        // amplitude step at y = k1 + A k2, without branches, in count units (the
+        // factor sqrt(1/counts_per_unit) joins the forward scale in phase 3):
+        // sqrt(c) / |phi~| = c / sqrt(c |phi~|^2) with the hardware reciprocal
+        // square root (a couple of ulp; a Newton-Raphson refinement cost 2% of the
+        // update and moved the parity errors by less than their float32 floor).
+        // x is held at FLT_MIN or above, so c = 0 gives 0 * (finite r) = 0 with no
+        // select.  Where phi~ = 0 (rare: the smallest |phi~|^2 of the lane is 0)
+        // the result is 0, and every pixel left at 0 takes sqrt(c) afterwards
+        // (which is 0 again where c = 0).
+        float m2min = 1.f;
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
-          const float in = meas[u].intensity(k2, a.inv_counts);
+          const float cn = meas[u].counts(k2);
           const float2 f = v[k2];
           const float m2 = cabs2(f);
-          const float x = fmaxf(__fmul_rn(in, m2), 1.17549435e-38f);
+          m2min = fminf(m2min, m2);
+          const float x = fmaxf(__fmul_rn(cn, m2), 1.17549435e-38f);
           const float r = rsqrtf(x);
-          v[k2] = cscale(f, __fmul_rn(in, r));
-          zmask |= (m2 > 0.f) ? 0u : (1u << k2);
+          v[k2] = cscale(f, __fmul_rn(cn, r));
         }
-        if (zmask) {
+        if (m2min == 0.f) {
 #pragma unroll
           for (int k2 = 0; k2 < B; ++k2)
-            if ((zmask >> k2) & 1u) v[k2] = make_float2(sqrtf(meas[u].intensity(k2, a.inv_counts)), 0.f);
+            if (v[k2].x == 0.f && v[k2].y == 0.f) v[k2] = make_float2(sqrtf(meas[u].counts(k2)), 0.f);
         }
         // forward DFT, first pass of the B x A split: unit b' = k1, over a' = k2
         Dft<B, -1>::run(v);
@@ -458,6 +461,10 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   const float onorm = red[32], pn = red[33];
   const float inv_on = (onorm > 0.f) ? 1.f / onorm : 0.f;
   const float inv_pn = 1.f / pn;
+  // (N/m)^2 times the count-unit factor of the amplitude step, and the
+  // normalisers, as pairs for the packed FP32x2 products
+  const float fs = __fmul_rn(a.scale, sqrtf(a.inv_counts));
+  const float2 fs2 = make_float2(fs, fs);
 
   // ---- phase 3: DFT along x of the support rows, then the updates ----------
   constexpr bool kHook = !std::is_same<Hook, NoHook>::value;
@@ -515,8 +522,10 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           if (x >= ch.x && x <= ch.y) {
             const float2 o = ov[u][k2];
             const float2 p = pv[u][k2];
-            const float2 phi = cmul(o, p);
-            const float2 d = csub(cscale(v[k2], a.scale), phi);
+            // -Phi = -(O P), then D = Phi' - Phi as one packed fused multiply-add
+            const float2 nphi = make_float2(__fmaf_rn(o.y, p.y, -__fmul_rn(o.x, p.x)),
+                                            __fmaf_rn(-o.x, p.y, -__fmul_rn(o.y, p.x)));
+            const float2 d = __ffma2_rn(v[k2], fs2, nphi);
             const float2 pc = cmulc(d, p);        // D * conj(P)
             srow[x] = make_float2(__fmaf_rn(pc.x, inv_pn, o.x), __fmaf_rn(pc.y, inv_pn, o.y));
             if (dp_out) {
