@@ -443,9 +443,11 @@ static __global__ void init_place_kernel(float2 *spec, const float2 *x, int m, i
 // that covers the support gives the same sums: each warp takes whole rows and
 // its lanes the aligned pixel pairs within the row's disc bound (disc = 1; else
 // the whole row), summed with 16-byte loads, two pairs and up to kMergeSlots
-// corrections of each in flight together, no table read first.  Rows are cut
-// into `parts` chunks; merge_rows does chunk `part` with the threads
-// [t0, t0 + nt) of the calling CTA(s) (t0 and nt multiples of 32).
+// corrections of each in flight together, no table read first.  Rows are dealt
+// to `parts` callers in turn (row r to part r mod parts, so that every part gets
+// wide rows of the disc's middle and narrow ones of its ends alike); merge_rows
+// does part `part` with the threads [t0, t0 + nt) of the calling CTA(s) (t0 and
+// nt multiples of 32).
 constexpr int kMergeSlots = 8;   // corrections loaded together
 constexpr int kMergePairs = 2;   // pixel pairs per lane in flight
 
@@ -453,14 +455,12 @@ __device__ __forceinline__ void merge_rows(float2 *__restrict__ pup, const float
                                            int part, int parts, int y_lo, int rows, int m, int slots, int disc,
                                            int t0, int nt) {
   if (ns <= 0) return;
-  const int rpp = (rows + parts - 1) / parts;
-  const int r0 = part * rpp, r1 = min(rows, r0 + rpp);
   const int hp = m / 2;                                   // pixel pairs per row
   const size_t mm2 = (size_t)m * m / 2;                   // float4 per pupil
   float4 *p = reinterpret_cast<float4 *>(pup + (size_t)t * m * m);
   const float4 *d = reinterpret_cast<const float4 *>(dpup + (size_t)t * slots * m * m);
   const int lane = t0 & 31, warp = t0 >> 5, warps = nt >> 5;
-  for (int r = r0 + warp; r < r1; r += warps) {
+  for (int r = part + parts * warp; r < rows; r += parts * warps) {
     const int by = y_lo + r;
     const int hw = disc ? disc_half_width(by, y_lo, rows) : m;
     const int plo = max(0, m / 2 - hw) >> 1, phi = min(m - 1, m / 2 + hw) >> 1;   // pairs touching the bound
