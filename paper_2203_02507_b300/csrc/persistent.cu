@@ -189,7 +189,10 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
   constexpr bool load_tw = MSEL == 0;   // mixed tile sides reload them per update
   // every CTA of the cluster merges its share of a completed wave; the leader
   // then releases the tile's next wave
-  auto merge_wave = [&](const PItem &it) {
+  // after_relaxed: the update before closed with a relaxed barrier, so a cluster
+  // barrier first orders this cluster's own corrections before the merge reads them
+  auto merge_wave = [&](const PItem &it, bool after_relaxed) {
+    if (after_relaxed) cl.sync();
     const JobArgs *mj = pa.jobs + it.job;
     if (mj->epry)
       merge_rows(const_cast<float2 *>(mj->u.pup), mj->u.dpup, it.ltile, it.width, (int)q, PC, mj->u.y_lo,
@@ -221,12 +224,13 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     if (!ready) {
       // the current entry may depend on the wave the previous update completes
       if (pending) {
+        cl.sync();                         // the update's writes (its closing barrier was relaxed)
         if (leader) {
           const int last = count_done(pa, s_item[prv]) ? 1 : 0;
           for (int r = 0; r < PC; ++r) *cl.map_shared_rank(&s_last0, r) = last;
         }
         cl.sync();
-        if (s_last0) merge_wave(s_item[prv]);
+        if (s_last0) merge_wave(s_item[prv], false);
         pending = false;
       }
       if (leader) {
@@ -287,35 +291,36 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const UpdateArgs &ua = INL == 2 ? pa.inl[0].u : INL == 1 ? pa.inl[job].u : s_args;
     if constexpr (MSEL == 64) {
-      run_update<P64, Img>(ua, item, smem, load_tw, true, hook);
+      run_update<P64, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 128) {
-      run_update<P128, Img>(ua, item, smem, load_tw, true, hook);
+      run_update<P128, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 192) {
-      run_update<P192, Img>(ua, item, smem, load_tw, true, hook);
+      run_update<P192, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 256) {
-      run_update<P256q, Img>(ua, item, smem, load_tw, true, hook);
+      run_update<P256q, Img>(ua, item, smem, load_tw, false, hook);
     } else {
       switch (INL ? pa.inl[INL == 2 ? 0 : job].m : pa.jobs[job].m) {
-        case 64: run_update<P64, Img>(ua, item, smem, load_tw, true, hook); break;
-        case 128: run_update<P128, Img>(ua, item, smem, load_tw, true, hook); break;
-        case 192: run_update<P192, Img>(ua, item, smem, load_tw, true, hook); break;
-        default: run_update<P256, Img>(ua, item, smem, load_tw, true, hook); break;
+        case 64: run_update<P64, Img>(ua, item, smem, load_tw, false, hook); break;
+        case 128: run_update<P128, Img>(ua, item, smem, load_tw, false, hook); break;
+        case 192: run_update<P192, Img>(ua, item, smem, load_tw, false, hook); break;
+        default: run_update<P256, Img>(ua, item, smem, load_tw, false, hook); break;
       }
     }
     // the update's closing cluster barrier published the hook's results
-    if (s_last) merge_wave(s_item[prv]);
+    if (s_last) merge_wave(s_item[prv], true);
     ready = s_ready != 0;
     pending = true;
   }
   // the last update's done count, and its wave's merge (not after an abort)
   if (pending && !aborted) {
     const int prv = (k + 2) % 3;
+    cl.sync();                             // the update's writes (its closing barrier was relaxed)
     if (leader) {
       const int last = count_done(pa, s_item[prv]) ? 1 : 0;
       for (int r = 0; r < PC; ++r) *cl.map_shared_rank(&s_last0, r) = last;
     }
     cl.sync();
-    if (s_last0) merge_wave(s_item[prv]);
+    if (s_last0) merge_wave(s_item[prv], false);
   }
 }
 

@@ -161,9 +161,11 @@ struct NoHook {
 // Shared memory: [twiddles 2m (not with Cfg::TG)][normaliser partials][inter R x W][exchange scratch].
 // load_tw = false keeps the twiddles of an earlier update with the same m.
 // ordered_end = true: the closing cluster barrier also orders this update's global
-// writes before whatever the cluster does next (the persistent kernel signals
-// completion right after); false: the barrier only keeps the CTAs' shared memory
-// alive until the cluster has read it, and the kernel's end orders the writes.
+// writes before whatever the cluster does next; false: the barrier only keeps the
+// CTAs' shared memory alive until the cluster has read it (with a hook, its warp
+// releases what the hook wrote into the CTAs' shared memory), and the kernel's
+// end or a later cluster barrier orders the global writes (the persistent kernel
+// counts an update done only after the next update's phase barriers).
 // hook(0) and hook(1) run on one thread (cluster rank 0, the first lane of the
 // last warp, whose groups have the fewest phase-3 rows): hook(0) before its
 // phase-3 rows (for requests whose answers it needs only later), hook(1) after
@@ -546,6 +548,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
   if constexpr (C > 1) {
     if (ordered_end) {
       cg::this_cluster().sync();
+    } else if (kHook && q == 0 && tid >= T - 32) {
+      // the hook's warp releases what the hook wrote into the CTAs' shared memory
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     } else {
       // relaxed arrive: no wait for this thread's global stores to drain
       asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
