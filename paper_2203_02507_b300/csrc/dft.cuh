@@ -200,4 +200,85 @@ struct Dft<12, S> {
   }
 };
 
+// dft4 of inputs of which only those in IN (bit i: a_i may be nonzero; the
+// others are exactly zero) and outputs of which only those in OUT are needed
+// (the others are left unspecified).  Every needed output is computed with the
+// operations of dft4<S> in the same order, minus the additions of zeros, so it
+// equals dft4<S>'s output (an exact-zero result may differ in its sign).
+template <int S, int IN, int OUT>
+__device__ __forceinline__ void dft4_band(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  constexpr bool i0 = IN & 1, i1 = IN & 2, i2 = IN & 4, i3 = IN & 8;
+  static_assert((i0 || i2) && (i1 || i3), "each half of the butterfly has a nonzero input");
+  auto neg = [](float2 z) { return make_float2(-z.x, -z.y); };
+  const float2 t0 = (i0 && i2) ? cadd(a0, a2) : i0 ? a0 : a2;
+  const float2 t1 = (i0 && i2) ? csub(a0, a2) : i0 ? a0 : neg(a2);
+  const float2 t2 = (i1 && i3) ? cadd(a1, a3) : i1 ? a1 : a3;
+  const float2 d = (i1 && i3) ? csub(a1, a3) : i1 ? a1 : neg(a3);
+  if constexpr ((OUT & 1) != 0) a0 = cadd(t0, t2);
+  if constexpr ((OUT & 4) != 0) a2 = csub(t0, t2);
+  if constexpr ((OUT & 2) != 0) a1 = cadd_si<S>(t1, d);
+  if constexpr ((OUT & 8) != 0) a3 = csub_si<S>(t1, d);
+}
+
+// Dft<16, S> for inputs that are zero outside [ILO, IHI] and outputs needed only
+// in [OLO, OHI] (a band of the line: the support of a disc in the middle of the
+// box).  The same butterflies, twiddles and order as Dft<16, S>, so the needed
+// outputs are its outputs; additions of the known zeros and the butterflies of
+// unneeded outputs are left out at compile time.
+template <int S, int ILO, int IHI, int OLO, int OHI>
+struct DftBand16 {
+  template <int N2>
+  static constexpr int in_mask() {
+    return ((N2 >= ILO && N2 <= IHI) ? 1 : 0) | ((N2 + 4 >= ILO && N2 + 4 <= IHI) ? 2 : 0) |
+           ((N2 + 8 >= ILO && N2 + 8 <= IHI) ? 4 : 0) | ((N2 + 12 >= ILO && N2 + 12 <= IHI) ? 8 : 0);
+  }
+  template <int K1>
+  static constexpr int out_mask() {
+    return ((K1 >= OLO && K1 <= OHI) ? 1 : 0) | ((K1 + 4 >= OLO && K1 + 4 <= OHI) ? 2 : 0) |
+           ((K1 + 8 >= OLO && K1 + 8 <= OHI) ? 4 : 0) | ((K1 + 12 >= OLO && K1 + 12 <= OHI) ? 8 : 0);
+  }
+  template <int N2>
+  __device__ __forceinline__ static void stage1(const float2 *v, float2 *y) {
+    float2 a0 = v[N2], a1 = v[4 + N2], a2 = v[8 + N2], a3 = v[12 + N2];
+    dft4_band<S, in_mask<N2>(), 15>(a0, a1, a2, a3);
+    y[N2 * 4 + 0] = a0;
+    y[N2 * 4 + 1] = a1;
+    y[N2 * 4 + 2] = a2;
+    y[N2 * 4 + 3] = a3;
+  }
+  template <int K1>
+  __device__ __forceinline__ static void stage2(const float2 *y, float2 *v) {
+    constexpr int om = out_mask<K1>();
+    if constexpr (om != 0) {
+      float2 a0 = y[K1], a1 = y[4 + K1], a2 = y[8 + K1], a3 = y[12 + K1];
+      dft4_band<S, 15, om>(a0, a1, a2, a3);
+      if constexpr ((om & 1) != 0) v[K1] = a0;
+      if constexpr ((om & 2) != 0) v[K1 + 4] = a1;
+      if constexpr ((om & 4) != 0) v[K1 + 8] = a2;
+      if constexpr ((om & 8) != 0) v[K1 + 12] = a3;
+    }
+  }
+  __device__ __forceinline__ static void run(float2 *v) {
+    float2 y[16];
+    stage1<0>(v, y);
+    stage1<1>(v, y);
+    stage1<2>(v, y);
+    stage1<3>(v, y);
+    // twiddles w16^{n2 k1}, as in Dft<16, S>
+    y[1 * 4 + 1] = mul_cs<S>(y[5], FPM_C8, FPM_S8);    // w^1
+    y[1 * 4 + 2] = mul_cs<S>(y[6], FPM_R2, FPM_R2);    // w^2
+    y[1 * 4 + 3] = mul_cs<S>(y[7], FPM_S8, FPM_C8);    // w^3
+    y[2 * 4 + 1] = mul_cs<S>(y[9], FPM_R2, FPM_R2);    // w^2
+    y[2 * 4 + 2] = mul_si<S>(y[10]);                   // w^4
+    y[2 * 4 + 3] = mul_cs<S>(y[11], -FPM_R2, FPM_R2);  // w^6
+    y[3 * 4 + 1] = mul_cs<S>(y[13], FPM_S8, FPM_C8);   // w^3
+    y[3 * 4 + 2] = mul_cs<S>(y[14], -FPM_R2, FPM_R2);  // w^6
+    y[3 * 4 + 3] = mul_cs<S>(y[15], -FPM_C8, -FPM_S8); // w^9
+    stage2<0>(y, v);
+    stage2<1>(y, v);
+    stage2<2>(y, v);
+    stage2<3>(y, v);
+  }
+};
+
 }  // namespace fpm

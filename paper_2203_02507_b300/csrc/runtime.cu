@@ -36,12 +36,52 @@ struct Variant {
   int m, a, b, tpt, c, t;
   UpdateKernel k_u16, k_f32;
   size_t (*smem)(int rows);
+  // the same variant with band pruning (UpdateCfg ZB = zb > 0), run where the
+  // plan's support fits the band; null where the variant has none
+  int zb = 0;
+  UpdateKernel kz_u16 = nullptr, kz_f32 = nullptr;
 };
 
 template <class Cfg>
 static Variant make_variant() {
   return Variant{Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, &update_kernel<Cfg, uint16_t>,
                  &update_kernel<Cfg, float>, &Cfg::smem_bytes};
+}
+
+template <class Cfg, int Z>
+using WithBand = UpdateCfg<Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, Cfg::MINB, Cfg::PF, Cfg::PR, Cfg::TG,
+                           Cfg::DS, Z>;
+
+// A variant with a band-pruned twin: ZB blocks of B samples at each end of the
+// box lie outside every support that the twin is run for.
+template <class Cfg, int Z>
+static Variant make_variant_band() {
+  Variant v = make_variant<Cfg>();
+  v.zb = Z;
+  v.kz_u16 = &update_kernel<WithBand<Cfg, Z>, uint16_t>;
+  v.kz_f32 = &update_kernel<WithBand<Cfg, Z>, float>;
+  return v;
+}
+
+// The kernel of variant v for images of dtype: the band-pruned twin where the
+// plan's support fits its band.
+static UpdateKernel variant_kernel(const Variant *v, int dtype, bool band_ok) {
+  if (v->zb > 0 && band_ok) return dtype == FPM_U16 ? v->kz_u16 : v->kz_f32;
+  return dtype == FPM_U16 ? v->k_u16 : v->k_f32;
+}
+
+// Band pruning of tile side m (3 blocks of B samples at each end for A = 16):
+// whether the plan's support rows and chords lie in the band.
+constexpr int kBandBlocks = 3;
+static bool plan_band_fits(const fpm_plan *p) {
+  const int a = image_split_a(p->m);
+  if (a != 16) return false;
+  int c_lo = p->m, c_hi = -1;
+  for (int by = p->y_lo; by <= p->y_hi; ++by) {
+    c_lo = std::min(c_lo, p->chord_lo[by]);
+    c_hi = std::max(c_hi, p->chord_hi[by]);
+  }
+  return band_fits(a, p->m / a, kBandBlocks, p->y_lo, p->y_hi, c_lo, c_hi);
 }
 
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
@@ -72,10 +112,12 @@ static const std::vector<Variant> &variants() {
   static const std::vector<Variant> v = {
       make_variant<Cfg64>(),   make_variant<Cfg64w>(),  make_variant<Cfg64c2>(), make_variant<Cfg64c4>(),  // 64
       make_variant<Cfg64e>(),
-      make_variant<Cfg128o>(), make_variant<Cfg128t>(), make_variant<Cfg128>(),  make_variant<Cfg128w>(),  // 128
+      make_variant_band<Cfg128o, kBandBlocks>(), make_variant_band<Cfg128t, kBandBlocks>(), make_variant<Cfg128>(),
+      make_variant<Cfg128w>(),                                                                           // 128
       make_variant<Cfg128e>(),
       make_variant<Cfg192h>(), make_variant<Cfg192o>(), make_variant<Cfg192>(),  make_variant<Cfg192c>(),  // 192
-      make_variant<Cfg256o>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(), make_variant<Cfg256w>(),
+      make_variant_band<Cfg256o, kBandBlocks>(), make_variant<Cfg256x>(), make_variant<Cfg256q>(),
+      make_variant<Cfg256w>(),
       make_variant<Cfg256>(),  make_variant<Cfg256e>()};                                                // 256
   return v;
 }
@@ -203,6 +245,7 @@ struct DeviceState {
   float inv_counts = 1.f;
   bool loaded = false;
   const Variant *var = nullptr;
+  bool band_ok = false;                            // the support fits the band-pruned kernels' band
   std::vector<StepDev> steps;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, int64_t> graph_launches;
@@ -289,6 +332,7 @@ int ensure_device_state(fpm_plan *p) {
   const int rows = p->y_hi - p->y_lo + 1;
   d->var = find_variant(p->m, rows);
   if (!d->var) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", p->m, rows);
+  d->band_ok = plan_band_fits(p);
   if (const char *env = getenv("FPM_WAVE_BRANCHES")) d->branches = std::max(1, std::min(kMaxBranches, atoi(env)));
   if (!persistent_fits(p->m, rows)) d->tuned_mode = FPM_RUN_WAVES;   // FPM_RUN_AUTO before any tuning
   const size_t T = p->n_tiles, n = p->n, m = p->m;
@@ -299,6 +343,12 @@ int ensure_device_state(fpm_plan *p) {
                                   (int)v.smem(rows)));
       FPM_CK(cudaFuncSetAttribute((const void *)v.k_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)v.smem(rows)));
+      if (v.zb > 0) {
+        FPM_CK(cudaFuncSetAttribute((const void *)v.kz_u16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)v.smem(rows)));
+        FPM_CK(cudaFuncSetAttribute((const void *)v.kz_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)v.smem(rows)));
+      }
     }
   if ((e = cudaMalloc((void **)&d->spec, T * n * n * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc((void **)&d->pup, T * m * m * sizeof(float2))) != cudaSuccess)
@@ -331,8 +381,10 @@ int ensure_device_state(fpm_plan *p) {
   FPM_CK(cudaMalloc((void **)&d->err, 4 * sizeof(unsigned)));
   FPM_CK(cudaMemset(d->err, 0, 4 * sizeof(unsigned)));
   const size_t smem = d->var->smem(rows);
-  FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FPM_CK(cudaFuncSetAttribute((const void *)d->var->k_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FPM_CK(cudaFuncSetAttribute((const void *)variant_kernel(d->var, FPM_U16, d->band_ok),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FPM_CK(cudaFuncSetAttribute((const void *)variant_kernel(d->var, FPM_F32, d->band_ok),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return FPM_OK;
 }
 
@@ -576,7 +628,7 @@ static int launch_update(fpm_plan *p, const UpdateArgs &a, long long item0, long
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = v->c > 1 ? 1 : 0;
-  UpdateKernel k = d->dtype == FPM_U16 ? v->k_u16 : v->k_f32;
+  UpdateKernel k = variant_kernel(v, d->dtype, d->band_ok);
   FPM_CK(cudaLaunchKernelEx(&cfg, k, a, item0));
   return FPM_OK;
 }

@@ -113,11 +113,16 @@ struct ImgCol {
 // addresses (mapa); 0: through generic pointers (map_shared_rank), which leaves
 // the register allocator more freedom where the update is inlined into a loop
 // with state of its own (the persistent kernel).
+// ZB_ > 0 (A = 16 only): the support lies in positions [ZB B, (A - ZB) B) of the
+// box in both directions (band_fits), so the radix-A passes that take support
+// samples skip their ZB zero blocks at each end, and those that give them
+// compute only the blocks in the band (DftBand16); 0: every block.
 template <int M_, int A_, int B_, int TPT_, int C_, int T_, int MINB_ = 1, int PF_ = 1, int PR_ = 0, int TG_ = 0,
-          int DS_ = 1>
+          int DS_ = 1, int ZB_ = 0>
 struct UpdateCfg {
   static constexpr int M = M_, A = A_, B = B_, TPT = TPT_, C = C_, T = T_, MINB = MINB_, PF = PF_, PR = PR_;
-  static constexpr int TG = TG_, DS = DS_;
+  static constexpr int TG = TG_, DS = DS_, ZB = ZB_;
+  static_assert(ZB == 0 || (A == 16 && 2 * ZB < A), "band pruning needs the radix-16 first pass");
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
   static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
@@ -133,6 +138,33 @@ struct UpdateCfg {
     return ((size_t)rows * W + (size_t)G * SCR + (TG ? 0 : 2 * M)) * sizeof(float2) + 64 * sizeof(float);
   }
 };
+
+// Whether a support of rows [y_lo, y_hi] and columns [c_lo, c_hi] lies in the
+// band of a ZB-pruned variant: positions [zb b, (a - zb) b) of the box.
+__host__ __device__ inline bool band_fits(int a, int b, int zb, int y_lo, int y_hi, int c_lo, int c_hi) {
+  const int lo = zb * b, hi = (a - zb) * b - 1;
+  return y_lo >= lo && y_hi <= hi && c_lo >= lo && c_hi <= hi;
+}
+
+// Whether block j of a radix-A pass over the support samples (positions
+// B j + lane) can hold a nonzero sample / a needed output.
+template <class Cfg>
+__device__ __forceinline__ constexpr bool in_band(int j) {
+  return Cfg::ZB == 0 || (j >= Cfg::ZB && j < Cfg::A - Cfg::ZB);
+}
+
+// The radix-A pass whose inputs are support samples (zero outside the band), and
+// the one whose outputs are (only those in the band are needed).
+template <class Cfg, int S>
+__device__ __forceinline__ void dft_a_in(float2 *v) {
+  if constexpr (Cfg::ZB > 0) DftBand16<S, Cfg::ZB, Cfg::A - 1 - Cfg::ZB, 0, 15>::run(v);
+  else Dft<Cfg::A, S>::run(v);
+}
+template <class Cfg, int S>
+__device__ __forceinline__ void dft_a_out(float2 *v) {
+  if constexpr (Cfg::ZB > 0) DftBand16<S, 0, 15, Cfg::ZB, Cfg::A - 1 - Cfg::ZB>::run(v);
+  else Dft<Cfg::A, S>::run(v);
+}
 
 // Twiddle i of a table: a shared-memory load, or a read-only global load (Cfg::TG).
 template <class Cfg>
@@ -241,7 +273,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
       for (int aa = 0; aa < A; ++aa) {
         const int x = B * aa + b;
-        const bool in = b < B && x >= ch.x && x <= ch.y;
+        const bool in = in_band<Cfg>(aa) && b < B && x >= ch.x && x <= ch.y;
         ov1[u][aa] = in ? srow[x] : make_float2(0.f, 0.f);
         pv1[u][aa] = in ? prow[x] : make_float2(0.f, 0.f);
       }
@@ -268,11 +300,13 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         float2 v[A];
 #pragma unroll
         for (int aa = 0; aa < A; ++aa) {
+          v[aa] = make_float2(0.f, 0.f);
+          if (!in_band<Cfg>(aa)) continue;        // zero outside the band
           omax = fmaxf(omax, cabs2(ov1[u][aa]));
           pmax = fmaxf(pmax, cabs2(pv1[u][aa]));
           v[aa] = cmul(ov1[u][aa], pv1[u][aa]);
         }
-        Dft<A, 1>::run(v);
+        dft_a_in<Cfg, 1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) {
           const float2 w = tw_at<Cfg>(twi, k1 * B + b);
@@ -379,8 +413,9 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         const float2 *col_base = inter + (b - y_lo) * W;   // row y = B aa + b is stored at i = y - y_lo
 #pragma unroll
         for (int aa = 0; aa < A; ++aa)
-          v[aa] = ((in_mask[u] >> aa) & 1u) ? col_base[aa * B * W + inter_swz(B * aa + b, c)] : make_float2(0.f, 0.f);
-        Dft<A, 1>::run(v);
+          v[aa] = (in_band<Cfg>(aa) && ((in_mask[u] >> aa) & 1u)) ? col_base[aa * B * W + inter_swz(B * aa + b, c)]
+                                                                 : make_float2(0.f, 0.f);
+        dft_a_in<Cfg, 1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) scr[b * (A + 1) + k1] = (k1 == 0) ? v[0] : cmul(v[k1], tw_at<Cfg>(twi, k1 * B + b));
       }
@@ -442,11 +477,11 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         float2 v[A];
 #pragma unroll
         for (int bb = 0; bb < A; ++bb) v[bb] = scr[bb * (B + 1) + kk];
-        Dft<A, -1>::run(v);
+        dft_a_out<Cfg, -1>(v);
         float2 *col_base = inter + (kk - y_lo) * W;
 #pragma unroll
         for (int k2 = 0; k2 < A; ++k2)
-          if ((out_mask[u] >> k2) & 1u) col_base[k2 * B * W + inter_swz(kk + B * k2, c)] = v[k2];
+          if (in_band<Cfg>(k2) && ((out_mask[u] >> k2) & 1u)) col_base[k2 * B * W + inter_swz(kk + B * k2, c)] = v[k2];
       }
     }
     __syncwarp(gmask);
@@ -486,7 +521,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
 #pragma unroll
       for (int k2 = 0; k2 < A; ++k2) {
         const int x = kk + B * k2;
-        const bool in = kk < B && x >= ch.x && x <= ch.y;
+        const bool in = in_band<Cfg>(k2) && kk < B && x >= ch.x && x <= ch.y;
         ov[u][k2] = in ? srow[x] : make_float2(0.f, 0.f);
         pv[u][k2] = in ? prow[x] : make_float2(0.f, 0.f);
       }
@@ -517,11 +552,11 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         float2 v[A];
 #pragma unroll
         for (int bb = 0; bb < A; ++bb) v[bb] = scr[bb * (B + 1) + kk];
-        Dft<A, -1>::run(v);
+        dft_a_out<Cfg, -1>(v);
 #pragma unroll
         for (int k2 = 0; k2 < A; ++k2) {
           const int x = kk + B * k2;
-          if (x >= ch.x && x <= ch.y) {
+          if (in_band<Cfg>(k2) && x >= ch.x && x <= ch.y) {
             const float2 o = ov[u][k2];
             const float2 p = pv[u][k2];
             // -Phi = -(O P), then D = Phi' - Phi as one packed fused multiply-add
