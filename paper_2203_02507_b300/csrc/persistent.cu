@@ -37,7 +37,8 @@ struct JobArgs {
   UpdateArgs u;     // the job's buffers; u.items unused
   int m;            // tile side
   int epry;
-  int pad0, pad1;
+  int band;         // the job's support fits the band of the band-pruned update
+  int pad1;
 };
 
 struct PItem {
@@ -160,7 +161,9 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
 // kernel parameters, indexed by the entry's job; 2: one job, whose arguments are
 // the inline table's first entry at a constant offset (the update then reads
 // them as immediate constant-bank operands, as in the wave launches).
-template <typename Img, int MSEL, int INL>
+// ZB: the band pruning of the update (MSEL = 128 or 256: every job's support
+// fits the band; with mixed tile sides each job's flag chooses).
+template <typename Img, int MSEL, int INL, int ZB>
 __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blocks<MSEL>())
     persistent_kernel(const __grid_constant__ PersistArgs pa) {
   constexpr int PC = persistent_cluster<MSEL>();
@@ -293,17 +296,25 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     if constexpr (MSEL == 64) {
       run_update<P64, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 128) {
-      run_update<P128, Img>(ua, item, smem, load_tw, false, hook);
+      run_update<WithBand<P128, ZB>, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 192) {
       run_update<P192, Img>(ua, item, smem, load_tw, false, hook);
     } else if constexpr (MSEL == 256) {
-      run_update<P256q, Img>(ua, item, smem, load_tw, false, hook);
+      run_update<WithBand<P256q, ZB>, Img>(ua, item, smem, load_tw, false, hook);
     } else {
-      switch (INL ? pa.inl[INL == 2 ? 0 : job].m : pa.jobs[job].m) {
+      const JobArgs &jb = INL ? pa.inl[INL == 2 ? 0 : job] : pa.jobs[job];
+      const bool band = jb.band != 0;
+      switch (jb.m) {
         case 64: run_update<P64, Img>(ua, item, smem, load_tw, false, hook); break;
-        case 128: run_update<P128, Img>(ua, item, smem, load_tw, false, hook); break;
+        case 128:
+          if (band) run_update<WithBand<P128, kBandBlocks>, Img>(ua, item, smem, load_tw, false, hook);
+          else run_update<P128, Img>(ua, item, smem, load_tw, false, hook);
+          break;
         case 192: run_update<P192, Img>(ua, item, smem, load_tw, false, hook); break;
-        default: run_update<P256, Img>(ua, item, smem, load_tw, false, hook); break;
+        default:
+          if (band) run_update<WithBand<P256, kBandBlocks>, Img>(ua, item, smem, load_tw, false, hook);
+          else run_update<P256, Img>(ua, item, smem, load_tw, false, hook);
+          break;
       }
     }
     // the update's closing cluster barrier published the hook's results
@@ -425,6 +436,7 @@ int refill_queue(QueueDev *q, const std::vector<QueueJob> &jobs, cudaStream_t st
     ja[j].u = plan_update_args(p);
     ja[j].m = p->m;
     ja[j].epry = p->epry ? 1 : 0;
+    ja[j].band = plan_band_fits(p) ? 1 : 0;
     smem = std::max(smem, persistent_smem(p->m, p->y_hi - p->y_lo + 1, msel));
   }
   if (smem > 232448) return fail(FPM_EINVAL, "a job's support is too large for the persistent kernel");
@@ -496,17 +508,20 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   // at most kInlineJobs jobs: their arguments from the kernel parameters (one job:
   // at constant offsets)
   const int inl = q->n_jobs == 1 ? 2 : q->n_jobs <= kInlineJobs ? 1 : 0;
-#define FPM_PK(M)                                                                                      \
-  (u16 ? (inl == 2 ? (K)&persistent_kernel<uint16_t, M, 2>                                             \
-                   : inl ? (K)&persistent_kernel<uint16_t, M, 1> : (K)&persistent_kernel<uint16_t, M, 0>) \
-       : (inl == 2 ? (K)&persistent_kernel<float, M, 2>                                                \
-                   : inl ? (K)&persistent_kernel<float, M, 1> : (K)&persistent_kernel<float, M, 0>))
+  // one tile side of 128 or 256 whose every job fits the band: the band-pruned update
+  bool band = q->n_jobs > 0;
+  for (const JobArgs &j : q->host_jobs) band = band && j.band;
+#define FPM_PK(M, Z)                                                                                         \
+  (u16 ? (inl == 2 ? (K)&persistent_kernel<uint16_t, M, 2, Z>                                                \
+                   : inl ? (K)&persistent_kernel<uint16_t, M, 1, Z> : (K)&persistent_kernel<uint16_t, M, 0, Z>) \
+       : (inl == 2 ? (K)&persistent_kernel<float, M, 2, Z>                                                   \
+                   : inl ? (K)&persistent_kernel<float, M, 1, Z> : (K)&persistent_kernel<float, M, 0, Z>))
   switch (q->msel) {
-    case 64: k = FPM_PK(64); break;
-    case 128: k = FPM_PK(128); break;
-    case 192: k = FPM_PK(192); break;
-    case 256: k = FPM_PK(256); break;
-    default: k = FPM_PK(0); break;
+    case 64: k = FPM_PK(64, 0); break;
+    case 128: k = band ? FPM_PK(128, kBandBlocks) : FPM_PK(128, 0); break;
+    case 192: k = FPM_PK(192, 0); break;
+    case 256: k = band ? FPM_PK(256, kBandBlocks) : FPM_PK(256, 0); break;
+    default: k = FPM_PK(0, 0); break;
   }
 #undef FPM_PK
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));

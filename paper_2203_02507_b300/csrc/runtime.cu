@@ -48,10 +48,6 @@ static Variant make_variant() {
                  &update_kernel<Cfg, float>, &Cfg::smem_bytes};
 }
 
-template <class Cfg, int Z>
-using WithBand = UpdateCfg<Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, Cfg::MINB, Cfg::PF, Cfg::PR, Cfg::TG,
-                           Cfg::DS, Z>;
-
 // A variant with a band-pruned twin: ZB blocks of B samples at each end of the
 // box lie outside every support that the twin is run for.
 template <class Cfg, int Z>
@@ -70,10 +66,9 @@ static UpdateKernel variant_kernel(const Variant *v, int dtype, bool band_ok) {
   return dtype == FPM_U16 ? v->k_u16 : v->k_f32;
 }
 
-// Band pruning of tile side m (3 blocks of B samples at each end for A = 16):
-// whether the plan's support rows and chords lie in the band.
-constexpr int kBandBlocks = 3;
-static bool plan_band_fits(const fpm_plan *p) {
+// Band pruning of tile side m (kBandBlocks blocks of B samples at each end for
+// A = 16): whether the plan's support rows and chords lie in the band.
+bool plan_band_fits(const fpm_plan *p) {
   const int a = image_split_a(p->m);
   if (a != 16) return false;
   int c_lo = p->m, c_hi = -1;

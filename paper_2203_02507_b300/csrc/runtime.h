@@ -93,6 +93,8 @@ const float2 *plan_spectra(const fpm_plan *p);
 // Slot of the plan's stitch tables (device memory freed with the plan; null
 // until the first stitch builds them), or null without device state.
 float2 **plan_stitch_tables(fpm_plan *p);
+// Whether the plan's support lies in the band of the band-pruned update kernels.
+bool plan_band_fits(const fpm_plan *p);
 // The plan's second stream for the stitch and its kStitchEvents events (made on
 // first use, destroyed with the plan).
 constexpr int kStitchEvents = 5;
