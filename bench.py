@@ -43,10 +43,10 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3      # 76.98 TFL
 # as it stands; a launch scales it by the updates it processes.  Emptied
 # whenever the kernel changes until re-captured.
 TRAFFIC_PER_UPDATE = {
-    # profiles/update_kernel_m256_4cta256_ncu_full.md: 12,635,904 + 0 B for 32 updates
-    ("waves", 256, 256, 4): (12635904 + 0) / 32,
-    # profiles/persistent_kernel_m256_ncu_full.md: 555,124,224 + 97,394,432 B for 3,600 updates
-    ("persistent", 256, 256, 4): (555124224 + 97394432) / 3600,
+    # profiles/update_kernel_m256_4cta256_ncu_full.md: 12,634,880 + 0 B for 32 updates
+    ("waves", 256, 256, 4): (12634880 + 0) / 32,
+    # profiles/persistent_kernel_m256_ncu_full.md: 553,616,128 + 94,384,896 B for 3,600 updates
+    ("persistent", 256, 256, 4): (553616128 + 94384896) / 3600,
 }
 
 EXTRA = {
