@@ -154,6 +154,9 @@ typedef struct {
   int32_t hr_overlap;           /* lines neighbouring tile objects share: overlap * (N/m) */
   int32_t fov_h, fov_w;         /* size of fpm_stitch's image: N + (tiles - 1)(N - hr_overlap) */
   int32_t tile_first;           /* grid index of the plan's tile 0 (0 for the whole grid) */
+  int32_t band;                 /* 1: the support lies in box positions [3 m/16, 13 m/16) in
+                                   both directions (m = 128, 256), so the update runs with
+                                   band-pruned radix-16 passes; 0: the general passes */
 } fpm_plan_info;
 
 /*

@@ -59,7 +59,7 @@ class PlanInfo(C.Structure):
         ("max_waves", C.c_int32), ("max_wave_width", C.c_int32), ("total_waves", C.c_int64),
         ("device_bytes", C.c_int64), ("cluster", C.c_int32), ("threads", C.c_int32),
         ("image_elems", C.c_int64), ("hr_overlap", C.c_int32), ("fov_h", C.c_int32), ("fov_w", C.c_int32),
-        ("tile_first", C.c_int32),
+        ("tile_first", C.c_int32), ("band", C.c_int32),
     ]
 
     def as_dict(self):

@@ -60,6 +60,7 @@ struct fpm_plan {
   std::vector<int32_t> chord_lo, chord_hi;   // [m], per box row; lo > hi when empty
   int32_t y_lo = 0, y_hi = -1;      // support rows (box coordinates)
   bool disc_ok = false;             // disc_half_width bounds every chord
+  bool band_ok = false;             // the support lies in the band-pruned update's band
   int32_t support_px = 0;
   int32_t max_waves = 0, max_width = 0;
   int64_t total_waves = 0;

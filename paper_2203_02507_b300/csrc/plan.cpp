@@ -122,6 +122,17 @@ static bool build_support(fpm_plan *p) {
     p->disc_ok = false;
     p->support_px = p->m * p->m;
   }
+  // band pruning: rows and every chord inside the band of the first radix-16 pass
+  const int a = image_split_a(p->m);
+  p->band_ok = false;
+  if (c > 0 && a == 16) {
+    int c_lo = p->m, c_hi = -1;
+    for (int by = p->y_lo; by <= p->y_hi; ++by) {
+      c_lo = std::min(c_lo, p->chord_lo[by]);
+      c_hi = std::max(c_hi, p->chord_hi[by]);
+    }
+    p->band_ok = band_fits(a, p->m / a, kBandBlocks, p->y_lo, p->y_hi, c_lo, c_hi);
+  }
   return c > 0;
 }
 
@@ -462,6 +473,7 @@ int fpm_plan_get_info(const fpm_plan *p, fpm_plan_info *info) {
   info->fov_h = (int32_t)(n + (p->tiles_y - 1) * (n - info->hr_overlap));
   info->fov_w = (int32_t)(n + (p->tiles_x - 1) * (n - info->hr_overlap));
   info->tile_first = p->tile_first;
+  info->band = p->band_ok ? 1 : 0;
   return FPM_OK;
 }
 

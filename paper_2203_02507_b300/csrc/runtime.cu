@@ -66,18 +66,9 @@ static UpdateKernel variant_kernel(const Variant *v, int dtype, bool band_ok) {
   return dtype == FPM_U16 ? v->k_u16 : v->k_f32;
 }
 
-// Band pruning of tile side m (kBandBlocks blocks of B samples at each end for
-// A = 16): whether the plan's support rows and chords lie in the band.
-bool plan_band_fits(const fpm_plan *p) {
-  const int a = image_split_a(p->m);
-  if (a != 16) return false;
-  int c_lo = p->m, c_hi = -1;
-  for (int by = p->y_lo; by <= p->y_hi; ++by) {
-    c_lo = std::min(c_lo, p->chord_lo[by]);
-    c_hi = std::max(c_hi, p->chord_hi[by]);
-  }
-  return band_fits(a, p->m / a, kBandBlocks, p->y_lo, p->y_hi, c_lo, c_hi);
-}
+// Whether the plan's support lies in the band of the band-pruned update kernels
+// (computed with the plan's support, fpm_plan_info.band).
+bool plan_band_fits(const fpm_plan *p) { return p->band_ok; }
 
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
 using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;

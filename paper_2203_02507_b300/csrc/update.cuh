@@ -139,20 +139,11 @@ struct UpdateCfg {
   }
 };
 
-// The configuration Cfg with band pruning Z, and the band the pruned variants
-// use: kBandBlocks blocks of B samples at each end (for m = 256 and 128 every
-// support of the configs lies inside).
+// The configuration Cfg with band pruning Z (kBandBlocks: for m = 256 and 128
+// every support of the configs lies in the band).
 template <class Cfg, int Z>
 using WithBand = UpdateCfg<Cfg::M, Cfg::A, Cfg::B, Cfg::TPT, Cfg::C, Cfg::T, Cfg::MINB, Cfg::PF, Cfg::PR, Cfg::TG,
                            Cfg::DS, Z>;
-constexpr int kBandBlocks = 3;
-
-// Whether a support of rows [y_lo, y_hi] and columns [c_lo, c_hi] lies in the
-// band of a ZB-pruned variant: positions [zb b, (a - zb) b) of the box.
-__host__ __device__ inline bool band_fits(int a, int b, int zb, int y_lo, int y_hi, int c_lo, int c_hi) {
-  const int lo = zb * b, hi = (a - zb) * b - 1;
-  return y_lo >= lo && y_hi <= hi && c_lo >= lo && c_hi <= hi;
-}
 
 // Whether block j of a radix-A pass over the support samples (positions
 // B j + lane) can hold a nonzero sample / a needed output.

@@ -30,6 +30,16 @@ __host__ __device__ inline int disc_half_width(int by, int y_lo, int rows) {
   return (int)sqrtf(h2 > 0.f ? h2 : 0.f) + 1;
 }
 
+// Band pruning of the update (tile sides whose first pass is radix 16): the
+// band is box positions [kBandBlocks B, (A - kBandBlocks) B) in both directions;
+// band_fits tells whether a support of rows [y_lo, y_hi] and columns
+// [c_lo, c_hi] lies inside it, so that the pruned kernels may run.
+constexpr int kBandBlocks = 3;
+__host__ __device__ inline bool band_fits(int a, int b, int zb, int y_lo, int y_hi, int c_lo, int c_hi) {
+  const int lo = zb * b, hi = (a - zb) * b - 1;
+  return y_lo >= lo && y_hi <= hi && c_lo >= lo && c_hi <= hi;
+}
+
 // The split of each supported tile side; every kernel for that side uses it.
 constexpr int image_split_a(int m) { return m == 64 ? 8 : m == 128 ? 16 : m == 192 ? 12 : m == 256 ? 16 : 0; }
 __host__ __device__ inline size_t tile_image_offset(int t, int l, int n_leds, int m) {

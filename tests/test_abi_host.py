@@ -156,6 +156,29 @@ def test_unmasked_epry_plan_covers_the_box(name, iters, tiles):
     masked.close()
 
 
+@pytest.mark.parametrize("name", ["tile64_plain", "fov2048_m256", "batch_m128", "batch_m192", "fov5120_m128"])
+def test_band_pruning_flag_follows_the_support(name):
+    """The update runs band-pruned radix-16 passes exactly when the tile side's
+    first pass is radix 16 (m = 128, 256) and the support (the oracle's pupil
+    support: its rows and its columns) lies in box positions [3 m/16, 13 m/16);
+    never for the unmasked update, whose support is the whole box."""
+    w = synth.WORKLOADS[name]
+    dz = synth.tile_defocus(w.n_tiles, *w.defocus_um, w.seed_offset)
+    g = _oracle_geometry(w, dz)
+    m = w.tile
+    rows = np.nonzero(g.support.any(axis=1))[0]
+    cols = np.nonzero(g.support.any(axis=0))[0]
+    lo, hi = 3 * m // 16, 13 * m // 16 - 1
+    want = m in (128, 256) and rows.min() >= lo and rows.max() <= hi and cols.min() >= lo and cols.max() <= hi
+    p = fpm.plan_for(w, defocus_um=dz, iters=1)
+    assert p.info["band"] == int(want)
+    p.close()
+    if w.epry:
+        q = fpm.plan_for(w, defocus_um=dz, iters=1, unmasked=True)
+        assert q.info["band"] == 0
+        q.close()
+
+
 def test_unmasked_flag_needs_epry():
     with pytest.raises(fpm.FpmError) as e:
         fpm.Plan(**_desc(unmasked=True))
