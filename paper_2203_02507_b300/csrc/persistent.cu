@@ -161,8 +161,8 @@ __device__ bool wait_for(const unsigned *flag, unsigned want, const unsigned *ab
 // kernel parameters, indexed by the entry's job; 2: one job, whose arguments are
 // the inline table's first entry at a constant offset (the update then reads
 // them as immediate constant-bank operands, as in the wave launches).
-// ZB: the band pruning of the update (MSEL = 128 or 256: every job's support
-// fits the band; with mixed tile sides each job's flag chooses).
+// ZB: the band pruning of the update for tiles of 128 and 256 (every such job's
+// support fits the band; other tile sides have no band-pruned form).
 template <typename Img, int MSEL, int INL, int ZB>
 __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blocks<MSEL>())
     persistent_kernel(const __grid_constant__ PersistArgs pa) {
@@ -302,19 +302,11 @@ __global__ void __launch_bounds__(persistent_threads<MSEL>(), persistent_min_blo
     } else if constexpr (MSEL == 256) {
       run_update<WithBand<P256q, ZB>, Img>(ua, item, smem, load_tw, false, hook);
     } else {
-      const JobArgs &jb = INL ? pa.inl[INL == 2 ? 0 : job] : pa.jobs[job];
-      const bool band = jb.band != 0;
-      switch (jb.m) {
+      switch (INL ? pa.inl[INL == 2 ? 0 : job].m : pa.jobs[job].m) {
         case 64: run_update<P64, Img>(ua, item, smem, load_tw, false, hook); break;
-        case 128:
-          if (band) run_update<WithBand<P128, kBandBlocks>, Img>(ua, item, smem, load_tw, false, hook);
-          else run_update<P128, Img>(ua, item, smem, load_tw, false, hook);
-          break;
+        case 128: run_update<WithBand<P128, ZB>, Img>(ua, item, smem, load_tw, false, hook); break;
         case 192: run_update<P192, Img>(ua, item, smem, load_tw, false, hook); break;
-        default:
-          if (band) run_update<WithBand<P256, kBandBlocks>, Img>(ua, item, smem, load_tw, false, hook);
-          else run_update<P256, Img>(ua, item, smem, load_tw, false, hook);
-          break;
+        default: run_update<WithBand<P256, ZB>, Img>(ua, item, smem, load_tw, false, hook); break;
       }
     }
     // the update's closing cluster barrier published the hook's results
@@ -508,9 +500,10 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
   // at most kInlineJobs jobs: their arguments from the kernel parameters (one job:
   // at constant offsets)
   const int inl = q->n_jobs == 1 ? 2 : q->n_jobs <= kInlineJobs ? 1 : 0;
-  // one tile side of 128 or 256 whose every job fits the band: the band-pruned update
+  // every job of tile side 128 or 256 fits the band: the band-pruned update for them
   bool band = q->n_jobs > 0;
-  for (const JobArgs &j : q->host_jobs) band = band && j.band;
+  for (const JobArgs &j : q->host_jobs)
+    if (j.m == 128 || j.m == 256) band = band && j.band;
 #define FPM_PK(M, Z)                                                                                         \
   (u16 ? (inl == 2 ? (K)&persistent_kernel<uint16_t, M, 2, Z>                                                \
                    : inl ? (K)&persistent_kernel<uint16_t, M, 1, Z> : (K)&persistent_kernel<uint16_t, M, 0, Z>) \
@@ -521,7 +514,7 @@ int launch_queue(QueueDev *q, unsigned *err, int stall_test, cudaStream_t st, in
     case 128: k = band ? FPM_PK(128, kBandBlocks) : FPM_PK(128, 0); break;
     case 192: k = FPM_PK(192, 0); break;
     case 256: k = band ? FPM_PK(256, kBandBlocks) : FPM_PK(256, 0); break;
-    default: k = FPM_PK(0, 0); break;
+    default: k = band ? FPM_PK(0, kBandBlocks) : FPM_PK(0, 0); break;
   }
 #undef FPM_PK
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem));
