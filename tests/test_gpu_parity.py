@@ -339,8 +339,10 @@ VARIANTS = {
 def test_update_kernel_variants_are_bit_identical(name, monkeypatch):
     """Every update-kernel variant of a tile side (threads per CTA, CTAs per
     cluster, CTAs per SM, lanes per transform, twiddles in shared or global
-    memory, row prefetch) runs the same per-row and per-column arithmetic: the
-    same state bit for bit, whichever variant the autotuner picks."""
+    memory, row prefetch, band-pruned passes or general ones: at m = 128 and 256
+    the first variants run pruned, 128x1 and 448x2 general) runs the same
+    per-row and per-column arithmetic: the same state, value for value,
+    whichever variant the autotuner picks."""
     j = job(name)
     outs = []
     for sel in VARIANTS[name]:
