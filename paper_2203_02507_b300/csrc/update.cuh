@@ -434,10 +434,11 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         // sqrt(c) / |phi~| = c / sqrt(c |phi~|^2) with the hardware reciprocal
         // square root (a couple of ulp; a Newton-Raphson refinement cost 2% of the
         // update and moved the parity errors by less than their float32 floor).
-        // x is held at FLT_MIN or above, so c = 0 gives 0 * (finite r) = 0 with no
-        // select.  Where phi~ = 0 (rare: the smallest |phi~|^2 of the lane is 0)
-        // the result is 0, and every pixel left at 0 takes sqrt(c) afterwards
-        // (which is 0 again where c = 0).
+        // x = c |phi~|^2 + FLT_MIN (one fused multiply-add; the FLT_MIN changes no
+        // value of x above 2^-102 and keeps x > 0), so c = 0 gives 0 * (finite r)
+        // = 0 with no select.  Where phi~ = 0 (rare: the smallest |phi~|^2 of the
+        // lane is 0) the result is 0, and every pixel left at 0 takes sqrt(c)
+        // afterwards (which is 0 again where c = 0).
         float m2min = 1.f;
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) {
@@ -445,7 +446,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const float2 f = v[k2];
           const float m2 = cabs2(f);
           m2min = fminf(m2min, m2);
-          const float x = fmaxf(__fmul_rn(cn, m2), 1.17549435e-38f);
+          const float x = __fmaf_rn(cn, m2, 1.17549435e-38f);
           const float r = rsqrtf(x);
           v[k2] = cscale(f, __fmul_rn(cn, r));
         }
