@@ -18,6 +18,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -218,7 +219,14 @@ extern "C" int fpm_update_tile_static(void *spectrum, int32_t n, void *pupil, in
   a.slots = 1;
   a.disc = fpm::disc_bound_covers(m, y_lo, y_hi, lo, hi) ? 1 : 0;
   a.err = nullptr;
-  if ((rc = fpm::launch_update_items(m, rows, FPM_F32, a, 0, 1, st))) return rc;
+  // the band-pruned update where the support fits its band, as a plan would run it
+  int c_lo = m, c_hi = -1;
+  for (int by = y_lo; by <= y_hi; ++by) {
+    c_lo = std::min(c_lo, lo[by]);
+    c_hi = std::max(c_hi, hi[by]);
+  }
+  const bool band = fa == 16 && fpm::band_fits(fa, fb, fpm::kBandBlocks, y_lo, y_hi, c_lo, c_hi);
+  if ((rc = fpm::launch_update_items(m, rows, FPM_F32, a, 0, 1, st, band))) return rc;
   const int disc = a.disc;
   if (epry && (rc = fpm::launch_merge(pup, d_dp, d_mg, 1, y_lo, rows, m, 1, disc, st))) return rc;
   return FPM_OK;

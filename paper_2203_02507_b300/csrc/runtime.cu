@@ -620,12 +620,12 @@ static int launch_update(fpm_plan *p, const UpdateArgs &a, long long item0, long
 }
 
 int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool band) {
   const Variant *v = find_variant(m, rows);
   if (!v) return fail(FPM_EINVAL, "no update kernel for tile %d with %d support rows", m, rows);
   if (count <= 0) return FPM_OK;
   const size_t smem = v->smem(rows);
-  UpdateKernel k = dtype == FPM_U16 ? v->k_u16 : v->k_f32;
+  UpdateKernel k = variant_kernel(v, dtype, band);
   FPM_CK(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(count * v->c), 1, 1);

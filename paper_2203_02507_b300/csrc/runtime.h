@@ -45,9 +45,10 @@ int run_persistent(fpm_plan *p, int32_t iters, cudaStream_t st, bool graph, bool
 bool update_variant(int m, int rows, int *a, int *b, int *cluster, int *threads);
 // Twiddle tables of the update kernel's two-pass split m = a * b (m entries each).
 void update_twiddles(int m, int a, int b, float2 *inv, float2 *fwd);
-// Launch the update kernel over items [item0, item0 + count) (image dtype FPM_U16 or FPM_F32).
+// Launch the update kernel over items [item0, item0 + count) (image dtype FPM_U16 or FPM_F32);
+// band: the support fits the band, so the variant's band-pruned twin runs where it has one.
 int launch_update_items(int m, int rows, int dtype, const UpdateArgs &a, long long item0, long long count,
-                        cudaStream_t st);
+                        cudaStream_t st, bool band = false);
 // The plan's device state (tables, spectra, pupils), created on first use.
 int ensure_device_state(fpm_plan *p);
 // Free the plan's online-ingestion state, if any (online.cu).
