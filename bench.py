@@ -819,7 +819,7 @@ def main():
         host_stack = torch.empty(stack.shape, dtype=stack.dtype, pin_memory=True)
         host_stack.copy_(stack)
         host_out = [torch.empty((w.n_tiles, w.hr, w.hr), dtype=torch.complex64, pin_memory=True) for _ in range(2)]
-        k_e2e = max(2, min(args.steps, 3))
+        k_e2e = max(2, args.steps)       # FOVs per plan; the stream fills and drains once over all of them
         # one FOV at a time
         plan.load_tiles(host_stack, k)
         plan.reconstruct(w.iters, mode=args.mode, graph=True)
