@@ -58,6 +58,9 @@ EXTRA = {
                                optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
     "ncu16_m256": synth.Workload("ncu16_m256", sensor=1024, tile=256, tiles=4, overlap=16, iters=1, epry=True,
                                  optics=synth.Optics(led_side=15), defocus_um=(-20.0, 20.0)),
+    # the 5120^2 job's kernel on 8 x 8 tiles of 128, 21 x 21 LEDs, one loop (925 MB of images)
+    "ncu64_m128": synth.Workload("ncu64_m128", sensor=1024, tile=128, tiles=8, overlap=0, iters=1, epry=True,
+                                 optics=synth.Optics(led_side=21), defocus_um=(-30.0, 30.0)),
 }
 
 

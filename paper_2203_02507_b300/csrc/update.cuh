@@ -125,7 +125,12 @@ struct UpdateCfg {
   static_assert(ZB == 0 || (A == 16 && 2 * ZB < A), "band pruning needs the radix-16 first pass");
   static constexpr int W = M / C;          // columns of "inter" held by one CTA
   static constexpr int G = T / TPT;        // transforms in flight per CTA
-  static constexpr int SCR = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
+  // exchange scratch of one group (complex values): the padded 2-D block, and for
+  // groups narrower than 16 lanes at m <= 128 a little more, so that the groups
+  // that share a warp start TPT banks apart (the groups' 8-byte accesses then
+  // fill a wavefront instead of landing on the same banks)
+  static constexpr int SCR0 = (B * (A + 1) > A * (B + 1)) ? B * (A + 1) : A * (B + 1);
+  static constexpr int SCR = (TPT < 16 && M <= 128) ? SCR0 + ((TPT - SCR0 % 16) % 16 + 16) % 16 : SCR0;
   static constexpr int UA = (B + TPT - 1) / TPT;   // units of the radix-A passes per lane
   static constexpr int UB = (A + TPT - 1) / TPT;   // units of the radix-B passes per lane
   static_assert(A * B == M, "m = A * B");
