@@ -669,8 +669,15 @@ int plan_stitch_streams(fpm_plan *p, cudaStream_t *aux, cudaEvent_t **ev) {
       return fail(FPM_ECUDA, "stitch stream creation failed");
     }
     for (cudaEvent_t &e : d->stitch_ev)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        // undo, so that the next call tries again from scratch
+        e = nullptr;
+        for (cudaEvent_t &x : d->stitch_ev)
+          if (x) cudaEventDestroy(x), x = nullptr;
+        cudaStreamDestroy(d->stitch_st);
+        d->stitch_st = nullptr;
         return fail(FPM_ECUDA, "stitch event creation failed");
+      }
   }
   *aux = d->stitch_st;
   *ev = d->stitch_ev;
