@@ -40,13 +40,22 @@ namespace cg = cooperative_groups;
 namespace fpm {
 
 
-// Swizzled position in "inter" (row length W) of local column p of stored row i,
-// which holds box row y: consecutive rows of one column and columns 16 apart
-// within one row fall in different banks.  The swizzle depends on y mod 16 only
-// through its low bits, so a lane that walks rows y = B a + b (B a multiple of
-// 8) keeps a constant or two-valued swizzle.
-__device__ __forceinline__ int inter_swz(int y, int p) { return p ^ ((y ^ (p >> 4)) & 15); }
-__device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz(y, p); }
+// Swizzled position in "inter" (row length W, a multiple of 16) of local column p
+// of stored row i, which holds box row y: the 4-bit XOR key (s y) ^ (p >> 4)
+// moves p within its aligned block of 16 columns.  A warp touches inter in two
+// patterns: TPT consecutive rows of 32 / TPT consecutive columns (the column
+// phase), and TPT consecutive columns of 32 / TPT consecutive rows (the row
+// phases).  With s = 1 for 16 lanes per transform and s = 4 for 8 or 4, both
+// patterns spread their 32 8-byte accesses evenly over the 16 bank pairs (two
+// wavefronts, the minimum).  A lane that walks rows y = B a + b (B a multiple of
+// 8) keeps a constant key.
+template <int TPT>
+__device__ __forceinline__ int inter_swz(int y, int p) {
+  constexpr int s = TPT >= 16 ? 1 : 4;
+  return p ^ (((s * y) ^ (p >> 4)) & 15);
+}
+template <int TPT>
+__device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz<TPT>(y, p); }
 
 // Accesses to a cluster CTA's shared memory through its 32-bit shared::cluster
 // address (mapa), not through a generic pointer.
@@ -335,8 +344,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = k1 + A * k2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          if constexpr (C > 1 && Cfg::DS) st_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at(i, by, p, W), v[k2]);
-          else inter_of[owner][inter_at(i, by, p, W)] = v[k2];
+          if constexpr (C > 1 && Cfg::DS) st_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at<TPT>(i, by, p, W), v[k2]);
+          else inter_of[owner][inter_at<TPT>(i, by, p, W)] = v[k2];
         }
       }
     }
@@ -417,7 +426,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         const float2 *col_base = inter + (b - y_lo) * W;   // row y = B aa + b is stored at i = y - y_lo
 #pragma unroll
         for (int aa = 0; aa < A; ++aa)
-          v[aa] = (in_band<Cfg>(aa) && ((in_mask[u] >> aa) & 1u)) ? col_base[aa * B * W + inter_swz(B * aa + b, c)]
+          v[aa] = (in_band<Cfg>(aa) && ((in_mask[u] >> aa) & 1u)) ? col_base[aa * B * W + inter_swz<TPT>(B * aa + b, c)]
                                                                  : make_float2(0.f, 0.f);
         dft_a_in<Cfg, 1>(v);
 #pragma unroll
@@ -486,7 +495,7 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
         float2 *col_base = inter + (kk - y_lo) * W;
 #pragma unroll
         for (int k2 = 0; k2 < A; ++k2)
-          if (in_band<Cfg>(k2) && ((out_mask[u] >> k2) & 1u)) col_base[k2 * B * W + inter_swz(kk + B * k2, c)] = v[k2];
+          if (in_band<Cfg>(k2) && ((out_mask[u] >> k2) & 1u)) col_base[k2 * B * W + inter_swz<TPT>(kk + B * k2, c)] = v[k2];
       }
     }
     __syncwarp(gmask);
@@ -541,8 +550,8 @@ __device__ __forceinline__ void run_update(const UpdateArgs &a, int4 item, float
           const int x = A * aa + b2;
           const int owner = (C > 1) ? x / W : 0;
           const int p = (C > 1) ? x - owner * W : x;
-          if constexpr (C > 1 && Cfg::DS) v[aa] = ld_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at(i, by, p, W));
-          else v[aa] = inter_of[owner][inter_at(i, by, p, W)];
+          if constexpr (C > 1 && Cfg::DS) v[aa] = ld_cluster(inter_cl[owner] + 8u * (uint32_t)inter_at<TPT>(i, by, p, W));
+          else v[aa] = inter_of[owner][inter_at<TPT>(i, by, p, W)];
         }
         Dft<B, -1>::run(v);
 #pragma unroll
