@@ -41,19 +41,25 @@ namespace fpm {
 
 
 // Swizzled position in "inter" (row length W, a multiple of 16) of local column p
-// of stored row i, which holds box row y: the 4-bit XOR key (s y) ^ (p >> 4)
-// moves p within its aligned block of 16 columns.  A warp touches inter in two
+// of stored row i, which holds box row y: the 4-bit XOR key h(y) ^ (p >> 4) moves
+// p within its aligned block of 16 columns.  A warp touches inter in two
 // patterns: TPT consecutive rows of 32 / TPT consecutive columns (the column
 // phase), and TPT consecutive columns of 32 / TPT consecutive rows (the row
-// phases).  With s = 1 for 16 lanes per transform and s = 4 for 8 or 4, both
-// patterns spread their 32 8-byte accesses evenly over the 16 bank pairs (two
-// wavefronts, the minimum).  A lane that walks rows y = B a + b (B a multiple of
-// 8) keeps a constant key.
+// phases).  8-byte accesses are served half a warp at a time, so each pattern is
+// free of bank conflicts when the 16 lanes of a half warp meet 16 different
+// bank pairs.  h(y) = y mod 16 does this for 16 lanes per transform; for 8,
+// h(y) = (y & 6) | (y & 1) << 3 (the columns of a half warp differ in bit 0, its
+// rows in bit 3); for 4, h(y) = 4 (y & 3) (columns in bits 0-1, rows in bits
+// 2-3).  A lane that walks rows y = B a + b (B a multiple of 8) keeps a constant
+// key.
 template <int TPT>
-__device__ __forceinline__ int inter_swz(int y, int p) {
-  constexpr int s = TPT >= 16 ? 1 : 4;
-  return p ^ (((s * y) ^ (p >> 4)) & 15);
+__device__ __forceinline__ int inter_key(int y) {
+  if constexpr (TPT >= 16) return y & 15;
+  else if constexpr (TPT == 8) return (y & 6) | ((y & 1) << 3);
+  else return (y & 3) << 2;
 }
+template <int TPT>
+__device__ __forceinline__ int inter_swz(int y, int p) { return p ^ ((inter_key<TPT>(y) ^ (p >> 4)) & 15); }
 template <int TPT>
 __device__ __forceinline__ int inter_at(int i, int y, int p, int w) { return i * w + inter_swz<TPT>(y, p); }
 
