@@ -71,10 +71,10 @@ static UpdateKernel variant_kernel(const Variant *v, int dtype, bool band_ok) {
 bool plan_band_fits(const fpm_plan *p) { return p->band_ok; }
 
 // candidates per tile side, preferred first; (m, A, B, lanes per transform, cluster, threads, min CTAs/SM)
-using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4>;
+using Cfg64 = UpdateCfg<64, 8, 8, 8, 1, 128, 4, 1, 0, 1>;
 using Cfg64w = UpdateCfg<64, 8, 8, 8, 1, 256, 2>;
 using Cfg64c2 = UpdateCfg<64, 8, 8, 8, 2, 128, 4, 1, 1>;
-using Cfg64c4 = UpdateCfg<64, 8, 8, 8, 4, 128, 4, 1, 1>;
+using Cfg64c4 = UpdateCfg<64, 8, 8, 8, 4, 128, 4, 1, 1, 1>;
 using Cfg128 = UpdateCfg<128, 16, 8, 8, 1, 128, 2>;
 using Cfg128w = UpdateCfg<128, 16, 8, 8, 1, 256, 1>;
 using Cfg128o = UpdateCfg<128, 16, 8, 8, 2, 256, 2, 1, 0, 1>;
