@@ -65,7 +65,8 @@ struct PersistArgs {
 };
 
 // 2-CTA clusters of 384 threads, one CTA per SM, for every tile side and for
-// mixed queues.  A queue whose jobs all have tiles of 256 runs the layout the
+// mixed queues, twiddles read through L1 (so that a mixed queue does not reload
+// them into shared memory for every update).  A queue whose jobs all have tiles of 256 runs the layout the
 // wave launches run: 4-CTA clusters of 256 threads (128 registers), two CTAs
 // of different clusters per SM, twiddles read through L1 and each column's
 // pixels fetched one column ahead.  The persistent configurations reach the
@@ -73,10 +74,10 @@ struct PersistArgs {
 // loop's state around the update, the explicit shared::cluster accesses cost
 // spills.
 constexpr int kPC = 2, kPT = 384, kPC256 = 4, kPT256 = 256;
-using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1, 1, 0, 0, 0>;
-using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1, 1, 0, 0, 0>;
-using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1, 1, 0, 0, 0>;
-using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1, 1, 0, 0, 0>;
+using P64 = UpdateCfg<64, 8, 8, 8, kPC, kPT, 1, 1, 0, 1, 0>;
+using P128 = UpdateCfg<128, 16, 8, 8, kPC, kPT, 1, 1, 0, 1, 0>;
+using P192 = UpdateCfg<192, 12, 16, 16, kPC, kPT, 1, 1, 0, 1, 0>;
+using P256 = UpdateCfg<256, 16, 16, 16, kPC, kPT, 1, 1, 0, 1, 0>;
 using P256q = UpdateCfg<256, 16, 16, 16, kPC256, kPT256, 2, 1, 0, 1, 0>;
 
 template <int MSEL>
